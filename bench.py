@@ -1,0 +1,373 @@
+#!/usr/bin/env python
+"""Throughput of the Tucker-FFT VIE operator product (Eq. 7-11) on GB300.
+
+One step = one batched operator product y = Kop x over nb right-hand sides
+(frequencies / ports) of the 256 x 256 x 8 thin-film meander over a ground
+plane with holes (seeded synthetic structure shaped like the paper's
+thin-film inductors): the Tucker restore of the kernel spectra (Eq. 10),
+the zero-padded forward 3-D FFT of the five basis grids, the 5 x 5 block
+multiply, the inverse FFT with truncation (Eq. 9), the two-fluid diagonal
+(Eq. 3, 22-23) and the incidence A / A^T apply (Eq. 7). FP32 complex is the
+headline; the FP64 product is timed on the same workload for comparison.
+
+Metric: voxel-matvecs/s = (sum over the batch of Kx*Ky*Kz) * steps / time.
+L2 is flushed (a 512 MB write) before every timed step; each step is timed
+by CUDA events on the library's stream.
+
+--impl reference times the CPU FP64 oracle (scipy.fft) on the same workload
+(one right-hand side per step) on the host cores; it is the only arm that
+runs the oracle besides the cpu_baseline block.
+
+Multi-GPU (torchrun): replicas only -- every rank runs its own batch (weak
+scaling); the ranks only exchange their timings.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "voxel-matvecs/s of Tucker-FFT VIE operator, FP32+refine vs FP64, % HBM peak"
+UNIT = "voxel-matvecs/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="svh", choices=["svh", "reference"])
+    p.add_argument("--nb", type=int, default=4, help="right-hand sides per step")
+    p.add_argument("--workload", default="meander256", choices=["meander256", "esfq512", "strip16"])
+    p.add_argument("--tucker-tol", type=float, default=1e-8)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-fp64", action="store_true")
+    return p.parse_args()
+
+
+def structure(name):
+    import svh_synth as S
+    if name == "meander256":
+        return S.meander_cfg2(), "meander 256x256x8 over a holed ground plane (seed 202), 0.1 um voxels"
+    if name == "esfq512":
+        return S.esfq_cfg5(), "eSFQ-like 512x512x24 multilayer block (seed 505), 0.5 um voxels"
+    return S.strip_cfg1(), "strip 16x16x4 (1024 voxels), 0.1 um"
+
+
+def dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as td
+        td.init_process_group("gloo")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as td
+        td.barrier()
+
+
+def allmax(ws, v):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as td
+    t = torch.tensor([float(v)], dtype=torch.float64)
+    td.all_reduce(t, op=td.ReduceOp.MAX)
+    return float(t.item())
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [l.strip().split(",") for l in self.f.read().splitlines() if l.strip()]
+        os.unlink(self.f.name)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax = float(r[2])
+                for n, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(n)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def pass_bytes(info, nb, csz):
+    """Algorithmic HBM bytes of each pass for one batched call (compulsory reads + writes)."""
+    K, M = info["K"], info["M"]
+    nza, nrows = info["n_active_planes"], info["n_active_rows"]
+    Kx, Px, Py = info["Kx"], info["Px"], info["Py"]
+    Ht = info["Hx"] * info["Hy"] * info["Hz"]
+    rows_line = 5 * nrows * Px * csz          # all active x-lines of one item, padded
+    planes = 5 * nza * Py * Px * csz          # all active planes after the y transform
+    vidx = 4 * nrows * Kx
+    return {
+        "tucker_rebuild": 7 * Ht * 4,
+        "x_fwd": nb * (5 * K * csz + rows_line) + vidx,
+        "y_fwd": nb * (rows_line + planes),
+        "z_pass": nb * 2 * planes + 7 * Ht * csz // 2,
+        "y_inv": nb * (planes + rows_line),
+        "x_inv_epilogue": nb * (rows_line + 5 * K * csz + 5 * K * csz + M * csz) + vidx + 40 * K,
+        "node_rows": nb * (5 * K * csz + M * csz) + 9 * M,
+    }
+
+
+def traffic_from_profiles(kernel, workload):
+    """DRAM bytes per launch recorded from ncu for this kernel and workload, if current."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"traffic_{workload}.txt")
+    if not os.path.exists(path):
+        return None
+    src = open(os.path.join(ROOT, "paper_2105_08627_gb300", "csrc", "matvec.cu"), "rb").read()
+    sha = hashlib.sha256(src).hexdigest()[:16]
+    vals = {}
+    for line in open(path):
+        if ":" in line and not line.startswith("#"):
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("matvec_cu_sha256_16") != sha:
+        return None
+    v = vals.get(f"{kernel}_dram_bytes_per_launch")
+    return float(v) if v else None
+
+
+def cpu_baseline(s, nb_cap=None, min_s=10.0, max_s=30.0):
+    """The oracle's FP64 FFT product timed on the host cores (bounded sample)."""
+    import svh_synth as S
+    from oracle import geometry as G
+    from oracle import greens as gr
+    from oracle import operator as op
+    g = G.build_grid(s)
+    P = (op.fft_size(g.Kx), op.fft_size(g.Ky), op.fft_size(g.Kz))
+    T = gr.toeplitz_octant(g.Kx, g.Ky, g.Kz)
+    S7 = op.spectra(gr.signed_from_octant(T), P)
+    cores = os.cpu_count()
+    x = S.random_complex(7, g.N)
+    om = 2 * np.pi * s.freqs[0]
+    op.apply_K_fft(g, S7, x, om, P, workers=cores)     # warm-up
+    n, t0 = 0, time.perf_counter()
+    while True:
+        op.apply_K_fft(g, S7, x, om, P, workers=cores)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= min_s or el + el / n > max_s:
+            break
+    return {"value": g.Kx * g.Ky * g.Kz * n / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n} single-vector FP64 products of the same structure (oracle: numpy + "
+                      f"scipy.fft workers={cores}), {el:.1f} s; kernel setup untimed"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist()
+    if rank != 0:
+        return 0
+    import svh_synth as S
+    from oracle import geometry as G
+    from oracle import greens as gr
+    from oracle import operator as op
+    s, desc = structure(args.workload)
+    g = G.build_grid(s)
+    P = (op.fft_size(g.Kx), op.fft_size(g.Ky), op.fft_size(g.Kz))
+    S7 = op.spectra(gr.signed_from_octant(gr.toeplitz_octant(g.Kx, g.Ky, g.Kz)), P)
+    cores = os.cpu_count()
+    x = S.random_complex(7, g.N)
+    om = 2 * np.pi * s.freqs[0]
+    for _ in range(args.warmup):
+        op.apply_K_fft(g, S7, x, om, P, workers=cores)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        op.apply_K_fft(g, S7, x, om, P, workers=cores)
+    el = time.perf_counter() - t0
+    Kt = g.Kx * g.Ky * g.Kz
+    val = Kt * args.steps / el
+    sample = (f"{args.steps} single-vector FP64 products (oracle: numpy + scipy.fft workers={cores}); "
+              f"one right-hand side per step instead of {args.nb}")
+    out = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128 (fp64 complex)",
+           "data": "synthetic",
+           "config": {"workload": desc, "Kx": g.Kx, "Ky": g.Ky, "Kz": g.Kz, "K": g.K, "N": g.N, "nb": 1,
+                      "precision": "fp64", "parallelism": f"replicas x{args.gpus}"},
+           "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+           "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def time_steps(h, torch, omega, x, y, steps, flush, profile=False):
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    if profile:
+        h.profile_begin(steps)
+    for k in range(steps):
+        flush.fill_(k & 0xFF)
+        evs[k][0].record()
+        h.matvec(omega, x, y)
+        evs[k][1].record()
+    torch.cuda.synchronize()
+    prof = h.profile_end() if profile else None
+    return sum(a.elapsed_time(b) for a, b in evs), prof
+
+
+def run_svh(args):
+    ws, rank, local = dist()
+    import torch
+
+    import svh_synth as S
+    from paper_2105_08627_gb300 import build, svh
+    torch.cuda.set_device(local)
+    build.build()
+    s, desc = structure(args.workload)
+    stream = torch.cuda.current_stream().cuda_stream
+    h = svh.Handle(local, stream)
+    h.setup_structure(s)
+    t_setup = time.perf_counter()
+    h.generate_toeplitz()
+    ranks = h.tucker_compress(args.tucker_tol)
+    h.set_kernel_mode(svh.SVH_KERNELS_TUCKER_REBUILD)
+    t_setup = time.perf_counter() - t_setup
+    info = h.info()
+    N, nb = info["N"], args.nb
+    Kt = info["Kx"] * info["Ky"] * info["Kz"]
+    omega = 2 * np.pi * s.freqs[0]
+    x = torch.from_numpy(S.random_complex(1000 + rank, (nb, N)).astype(np.complex64)).cuda()
+    y = torch.empty_like(x)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        h.matvec(omega, x, y)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clk = Clocks(local)
+    clk.start()
+    ms, _ = time_steps(h, torch, omega, x, y, args.steps, flush)
+    clocks = clk.stop()
+    ms = allmax(ws, ms)
+    value = ws * nb * Kt * args.steps / (ms / 1e3)
+    # per-pass durations (CUDA events on the library's stream) over a second identical region
+    _, (pass_ms, ncalls) = time_steps(h, torch, omega, x, y, args.steps, flush, profile=True)
+    pb = pass_bytes(info, nb, 8)
+    dom = max((k for k in pass_ms if k != "tucker_rebuild"), key=lambda k: pass_ms[k])
+    per_launch_ms = pass_ms[dom] / ncalls
+    peak, peak_kind = peaks()
+    achieved = pb[dom] / (per_launch_ms / 1e3) / 1e9
+    traffic = traffic_from_profiles(dom, args.workload)
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
+                "algorithmic_bytes_per_launch": pb[dom], "avg_launch_ms": per_launch_ms,
+                "share_of_step": pass_ms[dom] / sum(pass_ms.values()),
+                "pass_ms_per_step": {k: v / ncalls for k, v in pass_ms.items()},
+                "step_model_bytes": sum(pb.values()),
+                "step_model_frac": sum(pb.values()) / (ms / args.steps / 1e3) / 1e9 / peak}
+    # FP64 product on the same workload
+    fp64 = None
+    if not args.no_fp64:
+        x64 = x.to(torch.complex128)
+        y64 = torch.empty_like(x64)
+        for _ in range(2):
+            h.matvec(omega, x64, y64)
+        n64 = max(3, args.steps // 4)
+        ms64, _ = time_steps(h, torch, omega, x64, y64, n64, flush)
+        ms64 = allmax(ws, ms64)
+        fp64 = {"value": ws * nb * Kt * n64 / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64 / n64,
+                "steps": n64}
+        del x64, y64
+    # end to end through the host-memory entry point (pinned buffers, copies inside the timing)
+    e2e = None
+    if not args.no_e2e:
+        xh = torch.empty((nb, N), dtype=torch.complex64, pin_memory=True)
+        yh = torch.empty((nb, N), dtype=torch.complex64, pin_memory=True)
+        xh.copy_(x.cpu())
+        for _ in range(2):
+            h._ck(svh.lib().svh_matvec_host(h._h, omega, nb, svh._P(xh.data_ptr()), svh._P(yh.data_ptr()),
+                                            svh.SVH_FP32), "svh_matvec_host")
+        barrier(ws)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            h._ck(svh.lib().svh_matvec_host(h._h, omega, nb, svh._P(xh.data_ptr()), svh._P(yh.data_ptr()),
+                                            svh.SVH_FP32), "svh_matvec_host")
+        el = allmax(ws, time.perf_counter() - t0)
+        e2e = {"value": ws * nb * Kt * args.steps / el, "unit": UNIT,
+               "h2d_bytes_per_step": nb * N * 8, "d2h_bytes_per_step": nb * N * 8,
+               "entry_point": "svh_matvec_host (pinned host buffers)"}
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(s)
+    launches_per_step = 3 + 6
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "c64 (fp32 complex)", "data": "synthetic",
+               "config": {"workload": desc, "Kx": info["Kx"], "Ky": info["Ky"], "Kz": info["Kz"],
+                          "P": [info["Px"], info["Py"], info["Pz"]], "K": info["K"], "M": info["M"],
+                          "N": N, "nb": nb, "precision": "fp32", "kernel_spectra": "Tucker restore every step",
+                          "tucker_tol": args.tucker_tol, "tucker_ranks_G00": ranks[0].tolist(),
+                          "l2": "flushed before every step (512 MB write, outside the events)",
+                          "parallelism": f"replicas x{ws}", "setup_s": t_setup},
+               "fp64": fp64, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+               "gpu_launches": launches_per_step * args.steps, "clocks": clocks}
+        print(json.dumps(out), flush=True)
+    h.close()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_svh(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,202 @@
+/*
+ * svh.h -- C ABI of the GB300 library for the FFT-accelerated voxel VIE
+ * operator of SuperVoxHenry (arXiv 2105.08627).
+ *
+ * The library applies the operator of Eq. 7,
+ *
+ *     [ Z   -A^T ] [ I   ]
+ *     [ A    0   ] [ Phi ],
+ *
+ * where Z (Eq. 8) is the two-fluid diagonal (Eq. 3, 9, 16-18, 22-23) plus
+ * j*omega*mu*dx times Green's-function convolutions over the voxel grid,
+ * evaluated as in Eq. 9 by zero-padded 3-D FFTs whose kernel spectra are
+ * rebuilt from a Tucker representation (Eq. 10-11), and A is the face-node
+ * incidence matrix of current continuity (Eq. 7, Eq. 2).
+ *
+ * Conventions (all calls):
+ *  - Every call returns SVH_OK (0) or one of the SVH_ERR_* codes below; on
+ *    error svh_last_error() gives a message owned by the handle (valid until
+ *    the next call on that handle).
+ *  - Complex numbers are interleaved (re, im) pairs of float (SVH_FP32) or
+ *    double (SVH_FP64).
+ *  - Grid arrays are row-major with x fastest: index x + Kx*(y + Ky*z).
+ *  - Voxels (the K non-empty cells) are numbered in that raster order. Face
+ *    nodes are numbered by scanning voxels in order and, per voxel, its faces
+ *    in the order -x,+x,-y,+y,-z,+z: a face takes the next id the first time
+ *    it is met (a face shared by two voxels is one node).
+ *  - A vector of the operator has N = 5K + M entries laid out as
+ *    [I^x (K), I^y (K), I^z (K), I^2D (K), I^3D (K), Phi (M)].
+ *  - Pointer arguments ending in _dev are device pointers on the handle's
+ *    device, used in stream order on the handle's stream; all other pointers
+ *    are host memory, read or written before the call returns. The caller
+ *    keeps ownership of every array it passes; the library owns all of its
+ *    internal buffers and frees them in svh_destroy().
+ *  - A handle is not thread-safe: calls on one handle must not overlap.
+ *  - The seven unit kernels are indexed 0..6 = G00, Sx, Sy, Sz, Qx, Qy, Qz:
+ *    G00 couples constant moments, S_a a constant observer moment with the
+ *    source moment xi_a, Q_a the moments xi_a and xi'_a (App. A, Eq. 19-21).
+ *    They are dx-free (unit voxel, App. B): the library multiplies the
+ *    convolution by j*omega*mu*dx, which together with the basis
+ *    normalisation of Eq. 16-18 realises the dx^5 scale of App. B.
+ */
+#ifndef SVH_H
+#define SVH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct svh_handle svh_handle;
+
+#define SVH_OK                 0
+#define SVH_ERR_ARG            1  /* invalid argument or size mismatch */
+#define SVH_ERR_CUDA           2  /* a CUDA runtime call failed */
+#define SVH_ERR_OOM            3  /* device or host allocation failed */
+#define SVH_ERR_NOT_CONVERGED  4  /* iterative solve stopped above its tolerance */
+#define SVH_ERR_TIMEOUT        5  /* a bounded device wait ran out */
+#define SVH_ERR_SINGULAR       6  /* singular port matrix or preconditioner */
+#define SVH_ERR_STATE          7  /* call made before a prerequisite call */
+
+#define SVH_FP32 0
+#define SVH_FP64 1
+
+/* Kernel-spectrum modes for svh_set_kernel_mode(). */
+#define SVH_KERNELS_RESIDENT        0 /* octant spectra stay in HBM (default) */
+#define SVH_KERNELS_TUCKER_REBUILD  1 /* every FP32 matvec first rebuilds the spectra from
+                                         their Tucker cores and factors (Sec. II.B.2) */
+
+/* One port: a unit voltage source between the faces of its plus terminal and
+ * the faces of its minus terminal (Sec. II.A). Each face is encoded as
+ * voxel_linear_index*6 + face, face order -x,+x,-y,+y,-z,+z. */
+typedef struct {
+    int32_t n_plus;
+    const int32_t* plus;
+    int32_t n_minus;
+    const int32_t* minus;
+} svh_port;
+
+typedef struct {
+    int32_t Kx, Ky, Kz;        /* voxel grid */
+    int32_t Px, Py, Pz;        /* FFT sizes, each >= 2K_i - 1 (2K_i when smooth) */
+    int32_t Hx, Hy, Hz;        /* octant sizes P_i/2 + 1 of the stored spectra */
+    int64_t K, M, N;           /* non-empty voxels, face nodes, unknowns 5K+M */
+    int32_t nports;
+    int32_t n_fixed_nodes;     /* terminal nodes plus one gauge node per floating island */
+    int32_t n_active_planes;   /* z planes holding at least one voxel */
+    int32_t n_active_rows;     /* (z, y) rows holding at least one voxel */
+    double dx;                 /* voxel edge (m) */
+} svh_grid_info;
+
+/* Create a handle bound to CUDA device `device` and stream `stream`
+ * (a cudaStream_t; NULL means the legacy default stream). */
+int svh_create(svh_handle** h, int device, void* stream);
+int svh_destroy(svh_handle* h);
+const char* svh_last_error(const svh_handle* h);
+int svh_set_stream(svh_handle* h, void* stream);
+
+/* Voxel grid, materials and ports (Sec. II.A; Eq. 3 materials).
+ *  occ[Kz*Ky*Kx]   : 1 for a non-empty voxel, 0 otherwise;
+ *  lambda, sigma0  : London depth (m) and normal conductivity (S/m) per grid
+ *                    cell (read only at non-empty cells; lambda > 0 there);
+ *  ports[nports]   : terminal face lists (may be NULL when nports == 0).
+ * Builds the voxel list, face nodes, the implicit incidence A, the port
+ * terminals and gauge nodes, and picks FFT sizes. Errors: SVH_ERR_ARG for
+ * non-positive sizes or dx, an empty grid, lambda <= 0 on a voxel, or a port
+ * face on an empty voxel. Invalidates previously loaded kernels. */
+int svh_setup_grid(svh_handle* h, int Kx, int Ky, int Kz, double dx,
+                   const uint8_t* occ, const double* lambda, const double* sigma0,
+                   const svh_port* ports, int nports);
+/* Override the FFT sizes chosen by svh_setup_grid (each P_i >= 2K_i - 1 with
+ * prime factors 2, 3, 5, 7 only). Must precede the kernel calls below. */
+int svh_set_fft_sizes(svh_handle* h, int Px, int Py, int Pz);
+int svh_get_grid_info(const svh_handle* h, svh_grid_info* info);
+/* Face-node ids of every voxel, node[K*6] (for tests and post-processing). */
+int svh_get_nodes(const svh_handle* h, int32_t* node);
+
+/* Unit Toeplitz kernels (App. B, Eq. 19-21 and the off-diagonal blocks of
+ * Eq. 8) at the non-negative lattice offsets 0 <= d < K, T[7][Kz][Ky][Kx]
+ * (double). svh_generate_toeplitz computes them on the device by quadrature
+ * (Duffy transform at the singular offsets, Gauss-Legendre elsewhere);
+ * svh_load_toeplitz takes them from the caller. Either call also embeds them
+ * in the 2K circulant and transforms it (Eq. 9), storing the octant spectra
+ * described at svh_get_spectra. Requires svh_setup_grid. */
+int svh_generate_toeplitz(svh_handle* h);
+int svh_load_toeplitz(svh_handle* h, const double* T);
+int svh_get_toeplitz(const svh_handle* h, double* T);
+
+/* Octant spectra S[7][Hz][Hy][Hx] (double): the FFT of kernel u's circulant
+ * at frequency k is S_u(|k|) for the even kernels G00, Qx, Qy, Qz and
+ * -j*sign_a(k)*S_u(|k|) for S_a, with |k|_i = min(k_i, P_i - k_i) and
+ * sign_a(k) = +1 for k_a <= P_a/2, -1 otherwise. */
+int svh_get_spectra(const svh_handle* h, double* S);
+
+/* Tucker representation (Eq. 10) of kernel `kernel_id`'s octant spectrum:
+ * S = core x1 F1 x2 F2 x3 F3 with core[d3][d2][d1] (d1 index fastest),
+ * F1[Hx][d1], F2[Hy][d2], F3[Hz][d3] row-major (double). Loading switches
+ * that kernel to Tucker storage; svh_rebuild_spectra (or every FP32 matvec
+ * in SVH_KERNELS_TUCKER_REBUILD mode) restores it on the device (Eq. 11). */
+int svh_load_tucker(svh_handle* h, int kernel_id, int d1, int d2, int d3,
+                    const double* core, const double* F1, const double* F2, const double* F3);
+/* Algorithm 1 (Tucker-SVD, host) applied to the current octant spectra with
+ * truncation ||sigma_discarded|| <= tol/sqrt(3) * ||S||_F per mode; installs
+ * the result as by svh_load_tucker. ranks[7*3] (may be NULL) receives d1,d2,d3. */
+int svh_tucker_compress(svh_handle* h, double tol, int32_t* ranks);
+/* Copy out the Tucker data of one kernel; pass NULL arrays to query d1,d2,d3. */
+int svh_get_tucker(const svh_handle* h, int kernel_id, int32_t* d, double* core,
+                   double* F1, double* F2, double* F3);
+int svh_set_kernel_mode(svh_handle* h, int mode);
+/* Restore the FP32 octant spectra of all Tucker-stored kernels now (Eq. 10). */
+int svh_rebuild_spectra(svh_handle* h);
+
+/* y = Kop x for nb vectors (Eq. 7 with Z applied by Eq. 9):
+ *   rows of I:   y^beta = z^beta I^beta + j omega mu dx * (conv)^beta - (A^T Phi)^beta
+ *   rows of Phi: y = A I.
+ * x_dev, y_dev: nb*N complex values (interleaved) of the chosen precision,
+ * item b at offset b*N; x_dev and y_dev must not overlap. omega > 0 (rad/s).
+ * precision: SVH_FP32 (FFT and multiply in float, spectra in float) or
+ * SVH_FP64. Asynchronous on the handle's stream. Requires kernels. */
+int svh_matvec(svh_handle* h, double omega, int nb, const void* x_dev, void* y_dev,
+               int precision);
+/* Same product from and to host memory: copies x to the device, applies the
+ * operator and copies y back before returning (synchronous). */
+int svh_matvec_host(svh_handle* h, double omega, int nb, const void* x, void* y,
+                    int precision);
+
+/* ---- Per-pass timing of svh_matvec with CUDA events on the handle's stream.
+ * Passes: 0 Tucker rebuild (Eq. 10), 1 x-forward with gather, 2 y-forward,
+ * 3 z-FFT + block multiply + inverse z-FFT, 4 y-inverse, 5 x-inverse with
+ * the diagonal and A^T epilogue, 6 node rows (A I). svh_profile_begin
+ * starts recording for up to max_calls matvec calls (events are recorded
+ * without synchronising); svh_profile_end waits for them and returns the
+ * summed milliseconds per pass in ms[SVH_NPASS] and the calls recorded. */
+#define SVH_NPASS 7
+int svh_profile_begin(svh_handle* h, int max_calls);
+int svh_profile_end(svh_handle* h, double* ms, int* ncalls);
+
+/* ---- Host utilities (no device needed; safe to call on a machine without a GPU) */
+
+/* Voxel count and face-node numbering of an occupancy grid, with the
+ * conventions above. Call with node == NULL to learn K and M, then again with
+ * node[K*6]. */
+int svh_host_face_nodes(int Kx, int Ky, int Kz, const uint8_t* occ, int64_t* K_out, int64_t* M_out,
+                        int32_t* node);
+/* Octant spectra S[7][Pz/2+1][Py/2+1][Px/2+1] of the circulant embeddings of
+ * unit kernels T[7][Kz][Ky][Kx] (same definition as svh_get_spectra). */
+int svh_host_spectra(int Kx, int Ky, int Kz, int Px, int Py, int Pz, const double* T, double* S);
+/* Algorithm 1 (Tucker-SVD) of a real D1 x D2 x D3 array O stored with the
+ * mode-1 index fastest, O[(i3*D2 + i2)*D1 + i1]. The rank of mode i is the
+ * smallest d_i whose discarded singular values have 2-norm <= tol/sqrt(3) *
+ * ||O||_F, so ||O - restore||_F <= tol ||O||_F. Outputs (caller-allocated,
+ * worst-case sizes): d[3]; core[d3][d2][d1] (<= D1*D2*D3); F1[D1][d1] (<= D1*D1),
+ * F2[D2][d2], F3[D3][d3]. Singular values come from the eigenvalues of the
+ * unfoldings' Gram matrices (cyclic Jacobi). */
+int svh_host_tucker_svd(const double* O, int D1, int D2, int D3, double tol, int32_t* d, double* core,
+                        double* F1, double* F2, double* F3);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SVH_H */

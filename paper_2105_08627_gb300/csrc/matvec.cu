@@ -1,0 +1,447 @@
+// matvec.cu -- the FFT-accelerated operator product of Eq. 7 / Eq. 9 on the device.
+//
+// Per batch item the five basis grids I^alpha (alpha = x, y, z, 2D, 3D) are
+// zero-padded to Px x Py x Pz, transformed, multiplied point-wise by the
+// 5 x 5 block spectra (17 non-zero blocks built from 7 unit kernels) and
+// transformed back; only the K non-empty voxels are kept (Eq. 9):
+//
+//   pass 1  k_xfwd  : gather I^alpha rows from the voxel list, FFT along x      (Kx -> Px)
+//   pass 2  k_ycol  : FFT along y on tiles of contiguous kx columns             (Ky -> Py)
+//   pass 3  k_zpass : FFT along z, 5 x 5 block multiply, inverse FFT along z  (in place)
+//   pass 4  k_ycol  : inverse FFT along y, keep y < Ky                          (Py -> Ky)
+//   pass 5  k_xinv  : inverse FFT along x, keep x < Kx, then per voxel
+//                     y^beta = z^beta I^beta + j w mu dx/P conv - (A^T Phi)^beta (Eq. 7, 9)
+//   nodes   k_nodes : y_m = (A I)_m, the current-continuity rows of Eq. 7.
+//
+// Only z planes and (z, y) rows that hold voxels are stored or transformed:
+// the others are identically zero on input and not needed on output.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+
+#include "fft.cuh"
+#include "svh_internal.h"
+
+namespace svh {
+
+#ifndef SVH_NTHR
+#define SVH_NTHR 256
+#endif
+#ifndef SVH_PTS32
+#define SVH_PTS32 16
+#endif
+#ifndef SVH_PTS64
+#define SVH_PTS64 8
+#endif
+constexpr int NTHR = SVH_NTHR;
+template <typename T> struct Cfg;
+template <> struct Cfg<float> { static constexpr int MAXPTS = SVH_PTS32; };
+template <> struct Cfg<double> { static constexpr int MAXPTS = SVH_PTS64; };
+
+// outward flux of basis alpha (x, y, z, 2D, 3D) through face f (-x, +x, -y, +y, -z, +z)
+__constant__ float c_flux[5][6] = {
+    {-1.f, 1.f, 0.f, 0.f, 0.f, 0.f},
+    {0.f, 0.f, -1.f, 1.f, 0.f, 0.f},
+    {0.f, 0.f, 0.f, 0.f, -1.f, 1.f},
+    {0.5f, 0.5f, -0.5f, -0.5f, 0.f, 0.f},
+    {0.5f, 0.5f, 0.5f, 0.5f, -1.f, -1.f},
+};
+// diagonal scale s_beta of Eq. 9 / Eq. 16-18
+__constant__ double c_sbeta[5] = {1.0, 1.0, 1.0, 1.0 / 6.0, 0.5};
+
+template <typename C>
+__device__ __forceinline__ void load_twiddles(C* s, const C* __restrict__ g, int N) {
+    for (int i = threadIdx.x; i < N; i += blockDim.x) s[i] = g[i];
+}
+
+template <typename C> __device__ __forceinline__ C czero() { C c; c.x = 0; c.y = 0; return c; }
+
+// ------------------------------------------------------------------ pass 1
+template <typename T>
+__global__ void __launch_bounds__(NTHR) k_xfwd(
+    const typename CT<T>::type* __restrict__ x, int64_t Nvec, int64_t K,
+    const int32_t* __restrict__ vidx, const int32_t* __restrict__ rows, int nrows, int nza,
+    int Kx, int Ky, typename CT<T>::type* __restrict__ B1, FftPlan px,
+    const typename CT<T>::type* __restrict__ twg, int lpb, int64_t nlines) {
+    using C = typename CT<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* tw = reinterpret_cast<C*>(smem_raw);
+    const int N = px.N, ld = N + 1;
+    C* buf = tw + N;
+    const int64_t line0 = (int64_t)blockIdx.x * lpb;
+    const int nl = (int)min((int64_t)lpb, nlines - line0);
+    load_twiddles(tw, twg, N);
+    for (int i = threadIdx.x; i < nl * N; i += NTHR) {
+        int l = i / N, n = i - l * N;
+        int64_t line = line0 + l;
+        int64_t ba = line / nrows;
+        int ri = (int)(line - ba * nrows);
+        C v = czero<C>();
+        if (n < Kx) {
+            int vi = __ldg(vidx + (int64_t)rows[ri] * Kx + n);
+            if (vi >= 0) {
+                int64_t b = ba / 5, a = ba - 5 * b;
+                v = x[b * Nvec + a * K + vi];
+            }
+        }
+        buf[l * ld + n] = v;
+    }
+    __syncthreads();
+    fft_run<C, false, Cfg<T>::MAXPTS, ROWS>(buf, px, nl, ld, tw, threadIdx.x, NTHR);
+    for (int i = threadIdx.x; i < nl * N; i += NTHR) {
+        int l = i / N, n = i - l * N;
+        int64_t line = line0 + l;
+        int64_t ba = line / nrows;
+        int ri = (int)(line - ba * nrows);
+        B1[(ba * nza * Ky + rows[ri]) * (int64_t)N + n] = buf[l * ld + n];
+    }
+}
+
+// ------------------------------------------------------------------ passes 2 and 4
+// Forward: B1 [ba][zi][y<Ky][Px] -> B2 [ba][zi][Py][Px]; inverse: B2 -> B1 rows y < Ky.
+template <typename T, bool INV>
+__global__ void __launch_bounds__(NTHR) k_ycol(
+    const typename CT<T>::type* __restrict__ in, typename CT<T>::type* __restrict__ out,
+    int nza, int Ky, int Py, int Px, const uint8_t* __restrict__ rowmask, FftPlan py,
+    const typename CT<T>::type* __restrict__ twg, int tb) {
+    using C = typename CT<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* tw = reinterpret_cast<C*>(smem_raw);
+    C* buf = tw + Py;
+    const int kx0 = blockIdx.x * tb;
+    const int nt = min(tb, Px - kx0);
+    const int zi = blockIdx.y;
+    const int64_t ba = blockIdx.z;
+    const int64_t plane_in = (ba * nza + zi) * (int64_t)(INV ? Py : Ky);
+    const int64_t plane_out = (ba * nza + zi) * (int64_t)(INV ? Ky : Py);
+    const uint8_t* rm = rowmask + (int64_t)zi * Ky;
+    load_twiddles(tw, twg, Py);
+    for (int i = threadIdx.x; i < Py * tb; i += NTHR) {
+        int n = i / tb, t = i - n * tb;
+        C v = czero<C>();
+        if (t < nt) {
+            if (INV) v = in[(plane_in + n) * Px + kx0 + t];
+            else if (n < Ky && rm[n]) v = in[(plane_in + n) * Px + kx0 + t];
+        }
+        buf[i] = v;
+    }
+    __syncthreads();
+    fft_run<C, INV, Cfg<T>::MAXPTS, COLS>(buf, py, tb, tb, tw, threadIdx.x, NTHR);
+    const int nout = INV ? Ky : Py;
+    for (int i = threadIdx.x; i < nout * tb; i += NTHR) {
+        int n = i / tb, t = i - n * tb;
+        if (t < nt && (!INV || rm[n])) out[(plane_out + n) * Px + kx0 + t] = buf[n * tb + t];
+    }
+}
+
+// ------------------------------------------------------------------ pass 3
+template <typename T>
+__device__ __forceinline__ void block_multiply(typename CT<T>::type* io, T g, T sx, T sy, T sz, T qx, T qy, T qz) {
+    using C = typename CT<T>::type;
+    // spectra of the S kernels are -i*sign*R: mi(a) = -i a, pi(a) = +i a
+    auto mi = [](C a) { C c; c.x = a.y; c.y = -a.x; return c; };
+    auto pi = [](C a) { C c; c.x = -a.y; c.y = a.x; return c; };
+    C Ix = io[0], Iy = io[1], Iz = io[2], I2 = io[3], I3 = io[4];
+    C Yx = cadd(cscale(Ix, g), cscale(mi(cadd(I2, I3)), sx));
+    C Yy = cadd(cscale(Iy, g), cscale(mi(csub(I3, I2)), sy));
+    C Yz = cadd(cscale(Iz, g), cscale(pi(I3), (T)2 * sz));
+    C pX = pi(Ix), pY = pi(Iy), pZ = pi(Iz);
+    T qs = qx + qy, qd = qx - qy;
+    C Y2 = cadd(cadd(cscale(pX, sx), cscale(pY, -sy)), cadd(cscale(I2, qs), cscale(I3, qd)));
+    C Y3 = cadd(cadd(cscale(pX, sx), cscale(pY, sy)),
+                cadd(cscale(pZ, (T)-2 * sz), cadd(cscale(I2, qd), cscale(I3, qs + (T)4 * qz))));
+    io[0] = Yx; io[1] = Yy; io[2] = Yz; io[3] = Y2; io[4] = Y3;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NTHR) k_zpass(
+    typename CT<T>::type* __restrict__ B2, int nb, int nza, const int32_t* __restrict__ zlist,
+    int Pz, int Py, int Px, int Hx, int Hy, int Hz, const T* __restrict__ spec, FftPlan pz,
+    const typename CT<T>::type* __restrict__ twg, int tb) {
+    using C = typename CT<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* tw = reinterpret_cast<C*>(smem_raw);
+    C* buf = tw + Pz;
+    const int64_t b = blockIdx.x;
+    const int kx0 = blockIdx.y * tb;
+    const int nt = min(tb, Px - kx0);
+    const int ky = blockIdx.z;
+    const int ld = 5 * tb;
+    load_twiddles(tw, twg, Pz);
+    for (int i = threadIdx.x; i < Pz * ld; i += NTHR) buf[i] = czero<C>();
+    __syncthreads();
+    for (int i = threadIdx.x; i < 5 * nza * tb; i += NTHR) {
+        int t = i % tb;
+        int r = i / tb;
+        int zi = r % nza, a = r / nza;
+        if (t < nt) {
+            int z = zlist[zi];
+            buf[z * ld + a * tb + t] = B2[(((b * 5 + a) * nza + zi) * (int64_t)Py + ky) * Px + kx0 + t];
+        }
+    }
+    __syncthreads();
+    fft_run<C, false, Cfg<T>::MAXPTS, COLS>(buf, pz, ld, ld, tw, threadIdx.x, NTHR);
+    const int64_t Sk = (int64_t)Hx * Hy * Hz;
+    const int ay = min(ky, Py - ky);
+    const T sgy = (2 * ky <= Py) ? (T)1 : (T)-1;
+    for (int i = threadIdx.x; i < Pz * tb; i += NTHR) {
+        int kz = i / tb, t = i - kz * tb;
+        if (t >= nt) continue;
+        int kx = kx0 + t;
+        int ax = min(kx, Px - kx), az = min(kz, Pz - kz);
+        T sgx = (2 * kx <= Px) ? (T)1 : (T)-1;
+        T sgz = (2 * kz <= Pz) ? (T)1 : (T)-1;
+        int64_t off = ((int64_t)az * Hy + ay) * Hx + ax;
+        T g = __ldg(spec + off);
+        T sx = sgx * __ldg(spec + Sk + off);
+        T sy = sgy * __ldg(spec + 2 * Sk + off);
+        T sz = sgz * __ldg(spec + 3 * Sk + off);
+        T qx = __ldg(spec + 4 * Sk + off);
+        T qy = __ldg(spec + 5 * Sk + off);
+        T qz = __ldg(spec + 6 * Sk + off);
+        C io[5];
+#pragma unroll
+        for (int a = 0; a < 5; ++a) io[a] = buf[kz * ld + a * tb + t];
+        block_multiply<T>(io, g, sx, sy, sz, qx, qy, qz);
+#pragma unroll
+        for (int a = 0; a < 5; ++a) buf[kz * ld + a * tb + t] = io[a];
+    }
+    __syncthreads();
+    fft_run<C, true, Cfg<T>::MAXPTS, COLS>(buf, pz, ld, ld, tw, threadIdx.x, NTHR);
+    for (int i = threadIdx.x; i < 5 * nza * tb; i += NTHR) {
+        int t = i % tb;
+        int r = i / tb;
+        int zi = r % nza, a = r / nza;
+        if (t < nt) {
+            int z = zlist[zi];
+            B2[(((b * 5 + a) * nza + zi) * (int64_t)Py + ky) * Px + kx0 + t] = buf[z * ld + a * tb + t];
+        }
+    }
+}
+
+// ------------------------------------------------------------------ pass 5 + epilogue
+template <typename T>
+__global__ void __launch_bounds__(NTHR) k_xinv(
+    const typename CT<T>::type* __restrict__ B1, const typename CT<T>::type* __restrict__ x,
+    typename CT<T>::type* __restrict__ y, int64_t Nvec, int64_t K,
+    const int32_t* __restrict__ vidx, const int32_t* __restrict__ rows, int nrows, int nza,
+    int Kx, int Ky, const int32_t* __restrict__ node, const uint8_t* __restrict__ freem,
+    const double* __restrict__ lam, const double* __restrict__ sig0, double omega, double mu,
+    double dx, T conv_scale, int masked, FftPlan px, const typename CT<T>::type* __restrict__ twg,
+    int lpb, int64_t nlines) {
+    using C = typename CT<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* tw = reinterpret_cast<C*>(smem_raw);
+    const int N = px.N, ld = N + 1;
+    C* buf = tw + N;
+    const int64_t line0 = (int64_t)blockIdx.x * lpb;
+    const int nl = (int)min((int64_t)lpb, nlines - line0);
+    load_twiddles(tw, twg, N);
+    for (int i = threadIdx.x; i < nl * N; i += NTHR) {
+        int l = i / N, n = i - l * N;
+        int64_t line = line0 + l;
+        int64_t ba = line / nrows;
+        int ri = (int)(line - ba * nrows);
+        buf[l * ld + n] = B1[(ba * nza * Ky + rows[ri]) * (int64_t)N + n];
+    }
+    __syncthreads();
+    fft_run<C, true, Cfg<T>::MAXPTS, ROWS>(buf, px, nl, ld, tw, threadIdx.x, NTHR);
+    for (int i = threadIdx.x; i < nl * Kx; i += NTHR) {
+        int l = i / Kx, n = i - l * Kx;
+        int64_t line = line0 + l;
+        int64_t ba = line / nrows;
+        int ri = (int)(line - ba * nrows);
+        int vi = __ldg(vidx + (int64_t)rows[ri] * Kx + n);
+        if (vi < 0) continue;
+        int64_t b = ba / 5;
+        int be = (int)(ba - 5 * b);
+        const C* xb = x + b * Nvec;
+        C cv = buf[l * ld + n];
+        // j * conv_scale * conv
+        C val;
+        val.x = -conv_scale * cv.y;
+        val.y = conv_scale * cv.x;
+        // two-fluid diagonal: c = a + j omega mu b (Eq. 22-23), z^beta = c s_beta / dx
+        double lm = lam[vi], s0 = sig0[vi];
+        double wml2 = omega * mu * lm * lm;
+        double tt = s0 * wml2;
+        double den = 1.0 + tt * tt;
+        double ca = s0 * wml2 * wml2 / den;
+        double cb = omega * mu * (lm * lm / den);
+        double sc = c_sbeta[be] / dx;
+        T zr = (T)(ca * sc), zi_ = (T)(cb * sc);
+        C I = xb[be * K + vi];
+        val.x += zr * I.x - zi_ * I.y;
+        val.y += zr * I.y + zi_ * I.x;
+        // -(A^T Phi)^beta
+#pragma unroll
+        for (int f = 0; f < 6; ++f) {
+            float fl = c_flux[be][f];
+            if (fl != 0.f) {
+                int m = node[(int64_t)vi * 6 + f];
+                if (!masked || freem[m]) {
+                    C ph = xb[5 * K + m];
+                    val.x -= (T)fl * ph.x;
+                    val.y -= (T)fl * ph.y;
+                }
+            }
+        }
+        y[b * Nvec + be * K + vi] = val;
+    }
+}
+
+// ------------------------------------------------------------------ current-continuity rows
+template <typename T>
+__global__ void k_nodes(const typename CT<T>::type* __restrict__ x, typename CT<T>::type* __restrict__ y,
+                        int64_t Nvec, int64_t K, int64_t M, int nb, const int32_t* __restrict__ ninc,
+                        const uint8_t* __restrict__ freem, int masked) {
+    using C = typename CT<T>::type;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M * nb) return;
+    int64_t b = i / M, m = i - b * M;
+    const C* xb = x + b * Nvec;
+    C acc = czero<C>();
+    if (masked && !freem[m]) {
+        acc = xb[5 * K + m];
+    } else {
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            int code = ninc[m * 2 + e];
+            if (code < 0) continue;
+            int v = code / 6, f = code - 6 * v;
+#pragma unroll
+            for (int a = 0; a < 5; ++a) {
+                float fl = c_flux[a][f];
+                if (fl != 0.f) {
+                    C I = xb[a * K + v];
+                    acc.x += (T)fl * I.x;
+                    acc.y += (T)fl * I.y;
+                }
+            }
+        }
+    }
+    y[b * Nvec + 5 * K + m] = acc;
+}
+
+// ------------------------------------------------------------------ host launcher
+static FftPlan to_dev_plan(const FftPlanHost& p) {
+    FftPlan d{};
+    d.N = p.N;
+    d.nst = (int)p.R.size();
+    for (int i = 0; i < d.nst && i < MAX_STAGES; ++i) d.R[i] = p.R[i];
+    return d;
+}
+
+template <typename T>
+static int launch_matvec(Handle* h, double omega, int nb, const void* xv, void* yv, int masked) {
+    using C = typename CT<T>::type;
+    constexpr int MAXPTS = Cfg<T>::MAXPTS;
+    const C* x = static_cast<const C*>(xv);
+    C* y = static_cast<C*>(yv);
+    const int nza = (int)h->zlist.size();
+    const int nrows = (int)h->rows.size();
+    const int64_t K = h->K, M = h->M, Nvec = 5 * K + M;
+    const int Px = h->Px, Py = h->Py, Pz = h->Pz;
+    const size_t csz = sizeof(C);
+    // every FFT line (and the 5 basis lines of a z pencil) must fit one block's register staging
+    if (Px > MAXPTS * NTHR || Py > MAXPTS * NTHR || 5 * Pz > MAXPTS * NTHR)
+        return set_err(h, SVH_ERR_ARG, "svh_matvec: FFT size above the per-block limit of this build");
+    const size_t b1 = (size_t)nb * 5 * nza * h->Ky * Px * csz;
+    const size_t b2 = (size_t)nb * 5 * nza * (size_t)Py * Px * csz;
+    if (h->d_B1.bytes < b1) { int rc = dev_alloc(h, h->d_B1, b1); if (rc) return rc; }
+    if (h->d_B2.bytes < b2) { int rc = dev_alloc(h, h->d_B2, b2); if (rc) return rc; }
+    C* B1 = static_cast<C*>(h->d_B1.p);
+    C* B2 = static_cast<C*>(h->d_B2.p);
+    const int ti = std::is_same<T, float>::value ? 0 : 1;
+    const C* twx = static_cast<const C*>(ti == 0 ? h->d_tw32[0].p : h->d_tw64[0].p);
+    const C* twy = static_cast<const C*>(ti == 0 ? h->d_tw32[1].p : h->d_tw64[1].p);
+    const C* twz = static_cast<const C*>(ti == 0 ? h->d_tw32[2].p : h->d_tw64[2].p);
+    const T* spec = static_cast<const T*>(ti == 0 ? h->d_spec32.p : h->d_spec64.p);
+    FftPlan px = to_dev_plan(h->plan[0]), py = to_dev_plan(h->plan[1]), pz = to_dev_plan(h->plan[2]);
+    const int32_t* vidx = static_cast<const int32_t*>(h->d_vidx.p);
+    const int32_t* rows = static_cast<const int32_t*>(h->d_rows.p);
+    const uint8_t* d_rowmask = static_cast<const uint8_t*>(h->d_rowmask.p);
+
+    prof_mark(h, -1);
+    // pass 3 needs the spectra: rebuild them from Tucker first when asked (Eq. 10)
+    if (ti == 0 && h->kernel_mode == SVH_KERNELS_TUCKER_REBUILD) {
+        int rc = launch_tucker_rebuild(h);
+        if (rc) return rc;
+    }
+    prof_mark(h, 0);
+    // pass 1
+    {
+        int lpb = std::max(1, MAXPTS * NTHR / Px);
+        int64_t nlines = (int64_t)nb * 5 * nrows;
+        size_t sm = (size_t)(Px + lpb * (Px + 1)) * csz;
+        cudaFuncSetAttribute(k_xfwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        dim3 grid((unsigned)((nlines + lpb - 1) / lpb));
+        k_xfwd<T><<<grid, NTHR, sm, h->stream>>>(x, Nvec, K, vidx, rows, nrows, nza, h->Kx, h->Ky, B1,
+                                                 px, twx, lpb, nlines);
+    }
+    prof_mark(h, 1);
+    // pass 2
+    int tby = std::max(1, std::min(32, MAXPTS * NTHR / Py));
+    {
+        size_t sm = (size_t)(Py + Py * tby) * csz;
+        cudaFuncSetAttribute(k_ycol<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        dim3 grid((Px + tby - 1) / tby, nza, nb * 5);
+        k_ycol<T, false><<<grid, NTHR, sm, h->stream>>>(B1, B2, nza, h->Ky, Py, Px, d_rowmask, py, twy, tby);
+    }
+    prof_mark(h, 2);
+    // pass 3
+    {
+        int tbz = std::max(1, std::min(64, MAXPTS * NTHR / (5 * Pz)));
+        size_t sm = (size_t)(Pz + Pz * 5 * tbz) * csz;
+        cudaFuncSetAttribute(k_zpass<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        dim3 grid(nb, (Px + tbz - 1) / tbz, Py);
+        k_zpass<T><<<grid, NTHR, sm, h->stream>>>(B2, nb, nza, static_cast<const int32_t*>(h->d_zlist.p),
+                                                  Pz, Py, Px, h->Hx, h->Hy, h->Hz, spec, pz, twz, tbz);
+    }
+    prof_mark(h, 3);
+    // pass 4
+    {
+        size_t sm = (size_t)(Py + Py * tby) * csz;
+        cudaFuncSetAttribute(k_ycol<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        dim3 grid((Px + tby - 1) / tby, nza, nb * 5);
+        k_ycol<T, true><<<grid, NTHR, sm, h->stream>>>(B2, B1, nza, h->Ky, Py, Px, d_rowmask, py, twy, tby);
+    }
+    prof_mark(h, 4);
+    // pass 5 + epilogue
+    {
+        int lpb = std::max(1, MAXPTS * NTHR / Px);
+        int64_t nlines = (int64_t)nb * 5 * nrows;
+        size_t sm = (size_t)(Px + lpb * (Px + 1)) * csz;
+        cudaFuncSetAttribute(k_xinv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        const double mu = 4e-7 * 3.14159265358979323846;
+        T conv_scale = (T)(omega * mu * h->dx / ((double)Px * Py * Pz));
+        dim3 grid((unsigned)((nlines + lpb - 1) / lpb));
+        k_xinv<T><<<grid, NTHR, sm, h->stream>>>(
+            B1, x, y, Nvec, K, vidx, rows, nrows, nza, h->Kx, h->Ky,
+            static_cast<const int32_t*>(h->d_node.p), static_cast<const uint8_t*>(h->d_free.p),
+            static_cast<const double*>(h->d_lam.p), static_cast<const double*>(h->d_sig0.p), omega, mu,
+            h->dx, conv_scale, masked, px, twx, lpb, nlines);
+    }
+    prof_mark(h, 5);
+    // node rows
+    {
+        int64_t n = M * nb;
+        k_nodes<T><<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(
+            x, y, Nvec, K, M, nb, static_cast<const int32_t*>(h->d_ninc.p),
+            static_cast<const uint8_t*>(h->d_free.p), masked);
+    }
+    prof_mark(h, 6);
+    if (h->prof_on && h->prof_calls < h->prof_max) ++h->prof_calls;
+    SVH_CUDA_TRY(h, cudaGetLastError());
+    return SVH_OK;
+}
+
+int launch_matvec32(Handle* h, double omega, int nb, const void* x, void* y, int masked) {
+    return launch_matvec<float>(h, omega, nb, x, y, masked);
+}
+int launch_matvec64(Handle* h, double omega, int nb, const void* x, void* y, int masked) {
+    return launch_matvec<double>(h, omega, nb, x, y, masked);
+}
+
+}  // namespace svh

@@ -1,0 +1,103 @@
+// svh_internal.h -- handle state and helpers shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/svh.h"
+
+namespace svh {
+
+struct FftPlanHost {
+    int N = 0;
+    std::vector<int> R;
+};
+
+// Device arrays owned by a handle (freed in svh_destroy).
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+struct Tucker {
+    int d[3] = {0, 0, 0};
+    std::vector<double> core, F[3];
+};
+
+struct Handle {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+
+    // ---- grid (svh_setup_grid)
+    bool have_grid = false;
+    int Kx = 0, Ky = 0, Kz = 0, Px = 0, Py = 0, Pz = 0, Hx = 0, Hy = 0, Hz = 0;
+    double dx = 0;
+    int64_t K = 0, M = 0;
+    std::vector<int32_t> vox;         // grid linear index of each voxel
+    std::vector<int32_t> node;        // [K*6]
+    std::vector<double> lam, sig0;    // [K]
+    std::vector<int32_t> zlist;       // active planes (z values)
+    std::vector<int32_t> rows;        // active rows, zi*Ky + y
+    std::vector<uint8_t> fixed;       // [M] 1 for terminal/gauge nodes
+    std::vector<std::vector<int32_t>> port_plus, port_minus;   // node ids
+    std::vector<int32_t> gauge;
+
+    // device copies
+    DevBuf d_vidx;      // int32 [nza][Ky][Kx]  voxel index or -1
+    DevBuf d_rows;      // int32 [nrows]
+    DevBuf d_rowmask;   // uint8 [nza][Ky] 1 for rows holding voxels
+    DevBuf d_zlist;     // int32 [nza]
+    DevBuf d_node;      // int32 [K*6]
+    DevBuf d_ninc;      // int32 [M*2]  voxel*6+face touching each node, or -1
+    DevBuf d_free;      // uint8 [M] 1 for free nodes
+    DevBuf d_lam, d_sig0;   // double [K]
+
+    // ---- kernels
+    bool have_kernels = false;
+    std::vector<double> toep;          // [7][Kz][Ky][Kx]
+    std::vector<double> spec;          // [7][Hz][Hy][Hx]
+    DevBuf d_spec32, d_spec64;         // float / double [7][Hz][Hy][Hx]
+    DevBuf d_tw32[3], d_tw64[3];       // twiddles per axis
+    FftPlanHost plan[3];
+    bool tucker_on[7] = {false, false, false, false, false, false, false};
+    Tucker tk[7];
+    DevBuf d_tk_core[7], d_tk_F[7][3];   // float
+    DevBuf d_tk_w1, d_tk_w2;             // rebuild intermediates (float)
+    int kernel_mode = SVH_KERNELS_RESIDENT;
+
+    // ---- per-pass profiling (svh_profile_begin/end)
+    bool prof_on = false;
+    int prof_max = 0, prof_calls = 0;
+    std::vector<cudaEvent_t> prof_ev;   // [prof_max][SVH_NPASS + 1]
+
+    // ---- scratch for the matvec
+    DevBuf d_B1, d_B2;
+    DevBuf d_xin, d_yout;              // staging for svh_matvec_host
+};
+
+int set_err(Handle* h, int code, const std::string& msg);
+// record the event that closes pass p (p = -1 opens a call) when profiling
+void prof_mark(Handle* h, int p);
+int cuda_err(Handle* h, cudaError_t e, const char* what);
+int dev_alloc(Handle* h, DevBuf& b, size_t bytes);
+void dev_free(DevBuf& b);
+int dev_upload(Handle* h, DevBuf& b, const void* src, size_t bytes);
+
+// launchers (matvec.cu)
+int launch_matvec32(Handle* h, double omega, int nb, const void* x, void* y, int masked);
+int launch_matvec64(Handle* h, double omega, int nb, const void* x, void* y, int masked);
+// quadrature of the unit kernels (kernels_gen.cu): fills T[7][Kz][Ky][Kx] (host)
+int generate_toeplitz_device(Handle* h, std::vector<double>& T);
+// Tucker rebuild (tucker.cu)
+int launch_tucker_rebuild(Handle* h);
+
+}  // namespace svh
+
+#define SVH_CUDA_TRY(h, call)                                   \
+    do {                                                        \
+        cudaError_t e__ = (call);                               \
+        if (e__ != cudaSuccess) return svh::cuda_err((h), e__, #call); \
+    } while (0)

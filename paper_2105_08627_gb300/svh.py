@@ -1,0 +1,321 @@
+"""Thin ctypes binding of the C ABI in ``include/svh.h`` (argument marshalling only).
+
+Every computation runs in ``lib/libsvh.so``; this module converts NumPy arrays
+and torch tensors to pointers and raises :class:`SVHError` on a non-zero
+status. Importing it does not need a GPU; creating a :class:`Handle` does.
+If the library has not been built, :func:`lib` raises instead of falling
+back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libsvh.so")
+
+SVH_OK = 0
+SVH_ERR_ARG = 1
+SVH_ERR_CUDA = 2
+SVH_ERR_OOM = 3
+SVH_ERR_NOT_CONVERGED = 4
+SVH_ERR_TIMEOUT = 5
+SVH_ERR_SINGULAR = 6
+SVH_ERR_STATE = 7
+SVH_FP32 = 0
+SVH_FP64 = 1
+SVH_KERNELS_RESIDENT = 0
+SVH_KERNELS_TUCKER_REBUILD = 1
+KERNELS = ("G00", "Sx", "Sy", "Sz", "Qx", "Qy", "Qz")
+
+
+class SVHError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"svh error {code}: {msg}")
+        self.code = code
+
+
+class svh_port(C.Structure):
+    _fields_ = [("n_plus", C.c_int32), ("plus", C.POINTER(C.c_int32)),
+                ("n_minus", C.c_int32), ("minus", C.POINTER(C.c_int32))]
+
+
+class svh_grid_info(C.Structure):
+    _fields_ = [("Kx", C.c_int32), ("Ky", C.c_int32), ("Kz", C.c_int32),
+                ("Px", C.c_int32), ("Py", C.c_int32), ("Pz", C.c_int32),
+                ("Hx", C.c_int32), ("Hy", C.c_int32), ("Hz", C.c_int32),
+                ("K", C.c_int64), ("M", C.c_int64), ("N", C.c_int64),
+                ("nports", C.c_int32), ("n_fixed_nodes", C.c_int32),
+                ("n_active_planes", C.c_int32), ("n_active_rows", C.c_int32),
+                ("dx", C.c_double)]
+
+
+_P = C.c_void_p
+_DP = C.POINTER(C.c_double)
+_I32P = C.POINTER(C.c_int32)
+_I64P = C.POINTER(C.c_int64)
+_U8P = C.POINTER(C.c_uint8)
+
+# name -> (restype, argtypes); every symbol declared in include/svh.h
+SIGNATURES = {
+    "svh_create": (C.c_int, [C.POINTER(_P), C.c_int, _P]),
+    "svh_destroy": (C.c_int, [_P]),
+    "svh_last_error": (C.c_char_p, [_P]),
+    "svh_set_stream": (C.c_int, [_P, _P]),
+    "svh_setup_grid": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_double, _U8P, _DP, _DP,
+                                 C.POINTER(svh_port), C.c_int]),
+    "svh_set_fft_sizes": (C.c_int, [_P, C.c_int, C.c_int, C.c_int]),
+    "svh_get_grid_info": (C.c_int, [_P, C.POINTER(svh_grid_info)]),
+    "svh_get_nodes": (C.c_int, [_P, _I32P]),
+    "svh_generate_toeplitz": (C.c_int, [_P]),
+    "svh_load_toeplitz": (C.c_int, [_P, _DP]),
+    "svh_get_toeplitz": (C.c_int, [_P, _DP]),
+    "svh_get_spectra": (C.c_int, [_P, _DP]),
+    "svh_load_tucker": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, _DP, _DP, _DP, _DP]),
+    "svh_tucker_compress": (C.c_int, [_P, C.c_double, _I32P]),
+    "svh_get_tucker": (C.c_int, [_P, C.c_int, _I32P, _DP, _DP, _DP, _DP]),
+    "svh_set_kernel_mode": (C.c_int, [_P, C.c_int]),
+    "svh_rebuild_spectra": (C.c_int, [_P]),
+    "svh_matvec": (C.c_int, [_P, C.c_double, C.c_int, _P, _P, C.c_int]),
+    "svh_matvec_host": (C.c_int, [_P, C.c_double, C.c_int, _P, _P, C.c_int]),
+    "svh_profile_begin": (C.c_int, [_P, C.c_int]),
+    "svh_profile_end": (C.c_int, [_P, _DP, _I32P]),
+    "svh_host_face_nodes": (C.c_int, [C.c_int, C.c_int, C.c_int, _U8P, _I64P, _I64P, _I32P]),
+    "svh_host_spectra": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _DP, _DP]),
+    "svh_host_tucker_svd": (C.c_int, [_DP, C.c_int, C.c_int, C.c_int, C.c_double, _I32P, _DP, _DP, _DP, _DP]),
+}
+
+_lib = None
+
+
+def lib():
+    """Load lib/libsvh.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} not found: build it with "
+                               "`python -m paper_2105_08627_gb300.build` (no fallback exists)")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(_DP)
+
+
+def _i32p(a):
+    return a.ctypes.data_as(_I32P)
+
+
+def _check_host(rc, what):
+    if rc != SVH_OK:
+        raise SVHError(rc, what)
+
+
+# ---------------------------------------------------------------- host utilities
+def host_face_nodes(occ):
+    occ = np.ascontiguousarray(occ, np.uint8)
+    Kz, Ky, Kx = occ.shape
+    K = C.c_int64()
+    M = C.c_int64()
+    _check_host(lib().svh_host_face_nodes(Kx, Ky, Kz, occ.ctypes.data_as(_U8P), C.byref(K), C.byref(M), None),
+                "svh_host_face_nodes")
+    node = np.empty(K.value * 6, np.int32)
+    _check_host(lib().svh_host_face_nodes(Kx, Ky, Kz, occ.ctypes.data_as(_U8P), C.byref(K), C.byref(M),
+                                          _i32p(node)), "svh_host_face_nodes")
+    return node.reshape(K.value, 6), M.value
+
+
+def host_spectra(T, P):
+    T = np.ascontiguousarray(T, np.float64)
+    _, Kz, Ky, Kx = T.shape
+    Px, Py, Pz = P
+    S = np.empty((7, Pz // 2 + 1, Py // 2 + 1, Px // 2 + 1))
+    _check_host(lib().svh_host_spectra(Kx, Ky, Kz, Px, Py, Pz, _dp(T), _dp(S)), "svh_host_spectra")
+    return S
+
+
+def host_tucker_svd(O, tol):
+    """Algorithm 1 on O[D3, D2, D1] (mode 1 = last axis) -> (core[d3,d2,d1], [F1, F2, F3])."""
+    O = np.ascontiguousarray(O, np.float64)
+    D3, D2, D1 = O.shape
+    d = np.zeros(3, np.int32)
+    core = np.empty(O.size)
+    F = [np.empty(D * D) for D in (D1, D2, D3)]
+    _check_host(lib().svh_host_tucker_svd(_dp(O), D1, D2, D3, tol, _i32p(d), _dp(core), _dp(F[0]), _dp(F[1]),
+                                          _dp(F[2])), "svh_host_tucker_svd")
+    d1, d2, d3 = (int(v) for v in d)
+    return (core[:d1 * d2 * d3].reshape(d3, d2, d1).copy(),
+            [F[0][:D1 * d1].reshape(D1, d1).copy(), F[1][:D2 * d2].reshape(D2, d2).copy(),
+             F[2][:D3 * d3].reshape(D3, d3).copy()])
+
+
+# ---------------------------------------------------------------- handle
+class Handle:
+    """One library handle bound to a CUDA device and stream."""
+
+    def __init__(self, device=0, stream=None):
+        self._h = _P()
+        rc = lib().svh_create(C.byref(self._h), int(device), _P(stream or 0))
+        if rc != SVH_OK:
+            raise SVHError(rc, "svh_create failed (no CUDA device?)")
+
+    def _ck(self, rc, what=""):
+        if rc != SVH_OK:
+            msg = lib().svh_last_error(self._h)
+            raise SVHError(rc, f"{what}: {msg.decode() if msg else ''}")
+
+    def close(self):
+        if self._h:
+            lib().svh_destroy(self._h)
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        self._ck(lib().svh_set_stream(self._h, _P(stream or 0)), "svh_set_stream")
+
+    # -------------------------------------------------------- grid
+    def setup_grid(self, Kx, Ky, Kz, dx, occ, lam, sigma0, ports=()):
+        occ = np.ascontiguousarray(occ, np.uint8).ravel()
+        lam = np.ascontiguousarray(lam, np.float64).ravel()
+        sigma0 = np.ascontiguousarray(sigma0, np.float64).ravel()
+        keep = []
+        arr = (svh_port * max(1, len(ports)))()
+        for i, p in enumerate(ports):
+            plus = np.ascontiguousarray(p.plus if hasattr(p, "plus") else p[0], np.int32)
+            minus = np.ascontiguousarray(p.minus if hasattr(p, "minus") else p[1], np.int32)
+            keep += [plus, minus]
+            arr[i] = svh_port(plus.size, _i32p(plus), minus.size, _i32p(minus))
+        self._ck(lib().svh_setup_grid(self._h, Kx, Ky, Kz, dx, occ.ctypes.data_as(_U8P), _dp(lam), _dp(sigma0),
+                                      arr, len(ports)), "svh_setup_grid")
+
+    def setup_structure(self, s):
+        """Set up from an object with Kx, Ky, Kz, dx, occ, lam, sigma0, ports (e.g. svh_synth.Structure)."""
+        self.setup_grid(s.Kx, s.Ky, s.Kz, s.dx, s.occ, s.lam, s.sigma0, s.ports)
+
+    def set_fft_sizes(self, Px, Py, Pz):
+        self._ck(lib().svh_set_fft_sizes(self._h, Px, Py, Pz), "svh_set_fft_sizes")
+
+    def info(self):
+        gi = svh_grid_info()
+        self._ck(lib().svh_get_grid_info(self._h, C.byref(gi)), "svh_get_grid_info")
+        return {f: getattr(gi, f) for f, _ in svh_grid_info._fields_}
+
+    def nodes(self):
+        K = self.info()["K"]
+        out = np.empty(K * 6, np.int32)
+        self._ck(lib().svh_get_nodes(self._h, _i32p(out)), "svh_get_nodes")
+        return out.reshape(K, 6)
+
+    # -------------------------------------------------------- kernels
+    def generate_toeplitz(self):
+        self._ck(lib().svh_generate_toeplitz(self._h), "svh_generate_toeplitz")
+
+    def load_toeplitz(self, T):
+        i = self.info()
+        T = np.ascontiguousarray(T, np.float64)
+        if T.shape != (7, i["Kz"], i["Ky"], i["Kx"]):
+            raise ValueError(f"Toeplitz kernels must have shape (7, Kz, Ky, Kx), got {T.shape}")
+        self._ck(lib().svh_load_toeplitz(self._h, _dp(T)), "svh_load_toeplitz")
+
+    def toeplitz(self):
+        i = self.info()
+        T = np.empty((7, i["Kz"], i["Ky"], i["Kx"]))
+        self._ck(lib().svh_get_toeplitz(self._h, _dp(T)), "svh_get_toeplitz")
+        return T
+
+    def spectra(self):
+        i = self.info()
+        S = np.empty((7, i["Hz"], i["Hy"], i["Hx"]))
+        self._ck(lib().svh_get_spectra(self._h, _dp(S)), "svh_get_spectra")
+        return S
+
+    def load_tucker(self, u, core, Fs):
+        core = np.ascontiguousarray(core, np.float64)
+        d3, d2, d1 = core.shape
+        F1, F2, F3 = (np.ascontiguousarray(f, np.float64) for f in Fs)
+        self._ck(lib().svh_load_tucker(self._h, u, d1, d2, d3, _dp(core), _dp(F1), _dp(F2), _dp(F3)),
+                 "svh_load_tucker")
+
+    def tucker_compress(self, tol):
+        r = np.zeros(21, np.int32)
+        self._ck(lib().svh_tucker_compress(self._h, tol, _i32p(r)), "svh_tucker_compress")
+        return r.reshape(7, 3)
+
+    def get_tucker(self, u):
+        i = self.info()
+        d = np.zeros(3, np.int32)
+        self._ck(lib().svh_get_tucker(self._h, u, _i32p(d), None, None, None, None), "svh_get_tucker")
+        d1, d2, d3 = (int(v) for v in d)
+        core = np.empty((d3, d2, d1))
+        F1, F2, F3 = np.empty((i["Hx"], d1)), np.empty((i["Hy"], d2)), np.empty((i["Hz"], d3))
+        self._ck(lib().svh_get_tucker(self._h, u, _i32p(d), _dp(core), _dp(F1), _dp(F2), _dp(F3)),
+                 "svh_get_tucker")
+        return core, [F1, F2, F3]
+
+    def set_kernel_mode(self, mode):
+        self._ck(lib().svh_set_kernel_mode(self._h, mode), "svh_set_kernel_mode")
+
+    def rebuild_spectra(self):
+        self._ck(lib().svh_rebuild_spectra(self._h), "svh_rebuild_spectra")
+
+    # -------------------------------------------------------- operator
+    def matvec_ptr(self, omega, nb, x_ptr, y_ptr, precision):
+        self._ck(lib().svh_matvec(self._h, float(omega), int(nb), _P(x_ptr), _P(y_ptr), int(precision)),
+                 "svh_matvec")
+
+    def matvec(self, omega, x, y=None):
+        """y = Kop x for torch tensors on the handle's device (complex64 -> FP32, complex128 -> FP64).
+
+        x has shape (N,) or (nb, N); y (allocated when None) has the same shape."""
+        import torch
+        if not x.is_cuda or not x.is_contiguous():
+            raise ValueError("x must be a contiguous CUDA tensor")
+        prec = {torch.complex64: SVH_FP32, torch.complex128: SVH_FP64}.get(x.dtype)
+        if prec is None:
+            raise ValueError("x must be complex64 or complex128")
+        N = self.info()["N"]
+        nb = 1 if x.dim() == 1 else x.shape[0]
+        if x.numel() != nb * N:
+            raise ValueError(f"x must hold nb*N = {nb}*{N} values")
+        if y is None:
+            y = torch.empty_like(x)
+        self.matvec_ptr(omega, nb, x.data_ptr(), y.data_ptr(), prec)
+        return y
+
+    PASSES = ("tucker_rebuild", "x_fwd", "y_fwd", "z_pass", "y_inv", "x_inv_epilogue", "node_rows")
+
+    def profile_begin(self, max_calls):
+        self._ck(lib().svh_profile_begin(self._h, int(max_calls)), "svh_profile_begin")
+
+    def profile_end(self):
+        """-> (dict pass -> summed ms, number of calls recorded)."""
+        ms = np.zeros(len(self.PASSES))
+        n = C.c_int32()
+        self._ck(lib().svh_profile_end(self._h, _dp(ms), C.byref(n)), "svh_profile_end")
+        return dict(zip(self.PASSES, ms.tolist())), n.value
+
+    def matvec_host(self, omega, x):
+        """Host-memory product (copies in, applies, copies out); x complex64 or complex128 NumPy."""
+        x = np.ascontiguousarray(x)
+        prec = {np.complex64: SVH_FP32, np.complex128: SVH_FP64}.get(x.dtype.type)
+        if prec is None:
+            raise ValueError("x must be complex64 or complex128")
+        N = self.info()["N"]
+        nb = x.size // N
+        y = np.empty_like(x)
+        self._ck(lib().svh_matvec_host(self._h, float(omega), nb, x.ctypes.data_as(_P), y.ctypes.data_as(_P), prec),
+                 "svh_matvec_host")
+        return y

@@ -1,0 +1,224 @@
+"""GPU parity of the operator product (Eq. 7-9) against the CPU oracle, through the C ABI.
+
+Tolerances: FP64 path 1e-11 relative (quadrature of two independent kernel
+generators and FFT round-off); FP32 path 1e-5 relative in the 2-norm per
+batch item (the bound stated for the mixed-precision matvec), and every
+element within 2e-5 of the item's max-norm.
+"""
+import numpy as np
+import pytest
+
+import svh_synth as S
+from gpu_util import handle_for, oracle_reference, rel_err
+from oracle import greens as gr
+from oracle import operator as op
+
+pytestmark = pytest.mark.gpu
+
+FP32_TOL = 1e-5
+FP64_TOL = 1e-11
+
+
+def _torch():
+    import torch
+    assert torch.cuda.is_available()
+    return torch
+
+
+def _check_fp32(y, yref):
+    for b in range(yref.shape[0]):
+        assert rel_err(y[b], yref[b]) <= FP32_TOL, (b, rel_err(y[b], yref[b]))
+        assert np.abs(y[b] - yref[b]).max() <= 2 * FP32_TOL * np.abs(yref[b]).max()
+
+
+def test_device_toeplitz_matches_oracle():
+    for shape in [(16, 16, 4), (13, 9, 5), (41, 3, 2)]:
+        s = S.random_blob(7, *shape, fill=0.3)
+        h = handle_for(s)
+        T = h.toeplitz()
+        To = gr.toeplitz_octant(*shape)
+        scale = np.abs(To[0])
+        assert np.all(np.abs(T - To) <= 1e-12 * scale[None]), np.max(np.abs(T - To) / scale[None])
+        h.close()
+
+
+def test_grid_info_matches_oracle():
+    s = S.strip_cfg1()
+    h = handle_for(s)
+    g, _, P, _ = oracle_reference(s)
+    i = h.info()
+    assert (i["K"], i["M"], i["N"]) == (g.K, g.M, g.N) == (128, 488, 1128)
+    assert (i["Px"], i["Py"], i["Pz"]) == P
+    assert np.array_equal(h.nodes(), g.node)
+    h.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_strip_matvec_vs_dense_oracle(prec):
+    torch = _torch()
+    s = S.strip_cfg1()
+    g, S7, P, T = oracle_reference(s)
+    om = 2 * np.pi * 1e9
+    Kd = op.dense_K(g, gr.signed_from_octant(T), om)
+    nb = 3
+    x = S.random_complex(11, (nb, g.N))
+    yref = x @ Kd.T
+    h = handle_for(s)
+    dt = torch.complex128 if prec == "fp64" else torch.complex64
+    y = h.matvec(om, torch.from_numpy(x).to(dt).cuda()).cpu().numpy().astype(np.complex128)
+    if prec == "fp64":
+        for b in range(nb):
+            assert rel_err(y[b], yref[b]) <= FP64_TOL
+    else:
+        _check_fp32(y, yref)
+    h.close()
+
+
+@pytest.mark.parametrize("seed,shape,P", [
+    (21, (13, 9, 5), None),          # ragged, P = 26, 18, 10
+    (22, (37, 11, 3), None),         # 2*37 not smooth -> P = 75 = 3*5*5
+    (23, (24, 20, 6), (48, 40, 12)),
+    (24, (10, 14, 7), (21, 27, 14)),  # odd FFT sizes 2K - 1 (radix 3 and 7)
+    (25, (70, 33, 4), None),         # several x-lines per block, ragged y tiles
+])
+def test_random_blob_matvec_fp64_fp32(seed, shape, P):
+    torch = _torch()
+    s = S.random_blob(seed, *shape, fill=0.45)
+    g, S7, Pr, T = oracle_reference(s, P)
+    om = 2 * np.pi * 3e9
+    nb = 2
+    x = S.random_complex(seed, (nb, g.N))
+    yref = np.stack([op.apply_K_fft(g, S7, x[b], om, Pr) for b in range(nb)])
+    h = handle_for(s, toeplitz=T, P=P)
+    y64 = h.matvec(om, torch.from_numpy(x).cuda()).cpu().numpy()
+    for b in range(nb):
+        assert rel_err(y64[b], yref[b]) <= FP64_TOL
+    y32 = h.matvec(om, torch.from_numpy(x.astype(np.complex64)).cuda()).cpu().numpy().astype(np.complex128)
+    _check_fp32(y32, yref)
+    h.close()
+
+
+def test_empty_planes_and_rows():
+    """Planes and rows without voxels are skipped; the product must not change."""
+    torch = _torch()
+    s = S.random_blob(31, 12, 10, 8, fill=0.5)
+    s.occ[2:5] = 0
+    s.occ[:, 3:6, :] = 0
+    s.lam *= s.occ
+    s.sigma0 *= s.occ
+    g, S7, P, T = oracle_reference(s)
+    om = 2 * np.pi * 1e9
+    x = S.random_complex(3, (1, g.N))
+    yref = op.apply_K_fft(g, S7, x[0], om, P)[None]
+    h = handle_for(s, toeplitz=T)
+    assert h.info()["n_active_planes"] == 5
+    y = h.matvec(om, torch.from_numpy(x).cuda()).cpu().numpy()
+    assert rel_err(y[0], yref[0]) <= FP64_TOL
+    h.close()
+
+
+def test_matvec_host_equals_device():
+    torch = _torch()
+    s = S.random_blob(41, 9, 8, 3, fill=0.5)
+    h = handle_for(s)
+    N = h.info()["N"]
+    x = S.random_complex(5, (2, N))
+    for dt, npdt in ((torch.complex64, np.complex64), (torch.complex128, np.complex128)):
+        yd = h.matvec(2e9, torch.from_numpy(x.astype(npdt)).cuda()).cpu().numpy()
+        yh = h.matvec_host(2e9, x.astype(npdt))
+        assert np.array_equal(yd, yh)
+    h.close()
+
+
+def test_argument_errors():
+    torch = _torch()
+    from paper_2105_08627_gb300 import svh
+    h = svh.Handle(0)
+    s = S.strip_cfg1()
+    with pytest.raises(svh.SVHError) as e:
+        h.setup_grid(s.Kx, s.Ky, s.Kz, -1.0, s.occ, s.lam, s.sigma0, s.ports)
+    assert e.value.code == svh.SVH_ERR_ARG
+    h.setup_structure(s)
+    x = torch.zeros(h.info()["N"], dtype=torch.complex64, device="cuda")
+    with pytest.raises(svh.SVHError) as e:
+        h.matvec(1e9, x)
+    assert e.value.code == svh.SVH_ERR_STATE
+    h.generate_toeplitz()
+    with pytest.raises(svh.SVHError) as e:
+        h.matvec_ptr(-1.0, 1, x.data_ptr(), x.data_ptr(), svh.SVH_FP32)
+    assert e.value.code == svh.SVH_ERR_ARG
+    with pytest.raises(svh.SVHError) as e:      # x and y overlap
+        h.matvec_ptr(1e9, 1, x.data_ptr(), x.data_ptr(), svh.SVH_FP32)
+    assert e.value.code == svh.SVH_ERR_ARG
+    bad = s.ports[0].plus.copy()
+    bad[0] = 0                                   # voxel 0 of the grid is empty
+    with pytest.raises(svh.SVHError):
+        h.setup_grid(s.Kx, s.Ky, s.Kz, s.dx, s.occ, s.lam, s.sigma0, [(bad, s.ports[0].minus)])
+    h.close()
+
+
+def test_tucker_rebuild_matches_oracle_restore():
+    """a1: the device restore (Eq. 10) of Tucker data made by the oracle's Algorithm 1."""
+    torch = _torch()
+    from oracle import tucker as tk
+    from paper_2105_08627_gb300 import svh
+    s = S.random_blob(51, 24, 20, 6, fill=0.4)
+    h = handle_for(s)
+    spec = h.spectra()
+    for u in range(7):
+        C, Fs = tk.tucker_svd(np.transpose(spec[u], (2, 1, 0)), 1e-9)
+        h.load_tucker(u, np.transpose(C, (2, 1, 0)), Fs)
+    h.rebuild_spectra()
+    torch.cuda.synchronize()
+    # compare the FP32 matvec using rebuilt spectra with the oracle restore
+    g, S7, P, T = oracle_reference(s)
+    om = 2 * np.pi * 1e9
+    x = S.random_complex(8, (1, g.N))
+    yref = op.apply_K_fft(g, S7, x[0], om, P)[None]
+    y = h.matvec(om, torch.from_numpy(x.astype(np.complex64)).cuda()).cpu().numpy().astype(np.complex128)
+    _check_fp32(y, yref)
+    # rebuild-every-matvec mode gives the same result
+    h.set_kernel_mode(svh.SVH_KERNELS_TUCKER_REBUILD)
+    y2 = h.matvec(om, torch.from_numpy(x.astype(np.complex64)).cuda()).cpu().numpy().astype(np.complex128)
+    assert np.array_equal(y, y2)
+    h.close()
+
+
+def test_tucker_compress_error_bound():
+    torch = _torch()
+    from paper_2105_08627_gb300 import svh
+    s = S.random_blob(52, 30, 26, 5, fill=0.4)
+    h = handle_for(s)
+    spec = h.spectra()
+    ranks = h.tucker_compress(1e-6)
+    for u in range(7):
+        C, Fs = h.get_tucker(u)
+        rec = np.einsum("cba,ia,jb,kc->kji", C, Fs[0], Fs[1], Fs[2])
+        assert np.linalg.norm(rec - spec[u]) <= 1e-6 * np.linalg.norm(spec[u])
+        assert tuple(ranks[u]) == C.shape[::-1]
+    h.set_kernel_mode(svh.SVH_KERNELS_TUCKER_REBUILD)
+    g, S7, P, T = oracle_reference(s)
+    x = S.random_complex(9, (1, g.N))
+    yref = op.apply_K_fft(g, S7, x[0], 2e9, P)[None]
+    y = h.matvec(2e9, torch.from_numpy(x.astype(np.complex64)).cuda()).cpu().numpy().astype(np.complex128)
+    _check_fp32(y, yref)
+    h.close()
+
+
+@pytest.mark.slow
+def test_meander_256x256x8_full_size():
+    """cfg 2 size (256x256x8, P = 512x512x16) in the bench's launch shape: FP32 and FP64 vs the oracle."""
+    torch = _torch()
+    s = S.meander_cfg2()
+    g, S7, P, T = oracle_reference(s)
+    om = 2 * np.pi * 1e9
+    nb = 2
+    x = S.random_complex(202, (nb, g.N))
+    yref = np.stack([op.apply_K_fft(g, S7, x[b], om, P) for b in range(nb)])
+    h = handle_for(s)           # device-generated kernels: fully independent of the oracle
+    y64 = h.matvec(om, torch.from_numpy(x).cuda()).cpu().numpy()
+    for b in range(nb):
+        assert rel_err(y64[b], yref[b]) <= FP64_TOL
+    y32 = h.matvec(om, torch.from_numpy(x.astype(np.complex64)).cuda()).cpu().numpy().astype(np.complex128)
+    _check_fp32(y32, yref)
+    h.close()
