@@ -164,6 +164,29 @@ int svh_matvec(svh_handle* h, double omega, int nb, const void* x_dev, void* y_d
 int svh_matvec_host(svh_handle* h, double omega, int nb, const void* x, void* y,
                     int precision);
 
+/* ---- Product for callers that cannot allocate device memory at call time.
+ * (An interface of this library; the paper has no counterpart.)
+ * svh_matvec allocates its intermediate FFT grids with cudaMalloc the first
+ * time it sees a larger batch. A caller that may not allocate then -- a
+ * plug-in inside a host application that owns the device-memory budget, or
+ * a latency-critical loop that must not enter the allocator, which can
+ * synchronise the device -- can call svh_matvec_noalloc instead: the same
+ * product as svh_matvec with the same arguments, computed on a fixed scratch
+ * array of SVH_NOALLOC_SCRATCH_BYTES (64 MiB) compiled into the library's
+ * device code. Every GPU that loads the library holds that array until the
+ * process exits. The call makes no cudaMalloc/cudaFree and no allocating
+ * library call. Its first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream
+ * capture. The scratch needs 5 * nza * Px * (Ky + Py) complex values per
+ * right-hand side (nza = planes holding voxels); larger requests return
+ * SVH_ERR_ARG. All calls share the one array: calls that may run
+ * concurrently on the GPU (different streams or handles) race and must be
+ * serialised by the caller. Nothing in the array needs clearing between
+ * calls: every value a call reads it has written itself. It uses the
+ * resident spectra and never runs the per-product Tucker restore. */
+#define SVH_NOALLOC_SCRATCH_BYTES (64u << 20)
+int svh_matvec_noalloc(svh_handle* h, double omega, int nb, const void* x_dev, void* y_dev, int precision);
+
 /* ---- Per-pass timing of svh_matvec with CUDA events on the handle's stream.
  * Passes: 0 Tucker rebuild (Eq. 10), 1 x-forward with gather, 2 y-forward,
  * 3 z-FFT + block multiply + inverse z-FFT, 4 y-inverse, 5 x-inverse with

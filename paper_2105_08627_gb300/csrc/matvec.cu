@@ -333,8 +333,19 @@ static FftPlan to_dev_plan(const FftPlanHost& p) {
     return d;
 }
 
+// Bytes of the two intermediate grids for nb items: B1 holds the active
+// x-lines after the x transform, B2 the active planes after the y transform.
+void matvec_scratch_bytes(const Handle* h, int nb, int precision, size_t* b1, size_t* b2) {
+    const size_t csz = precision == SVH_FP32 ? 8 : 16;
+    const size_t nza = h->zlist.size();
+    *b1 = (size_t)nb * 5 * nza * h->Ky * h->Px * csz;
+    *b2 = (size_t)nb * 5 * nza * (size_t)h->Py * h->Px * csz;
+}
+
+// The launch sequence on caller-provided intermediate grids B1, B2.
 template <typename T>
-static int launch_matvec(Handle* h, double omega, int nb, const void* xv, void* yv, int masked) {
+static int run_matvec(Handle* h, double omega, int nb, const void* xv, void* yv, int masked, void* B1v,
+                      void* B2v, bool allow_rebuild) {
     using C = typename CT<T>::type;
     constexpr int MAXPTS = Cfg<T>::MAXPTS;
     const C* x = static_cast<const C*>(xv);
@@ -347,12 +358,8 @@ static int launch_matvec(Handle* h, double omega, int nb, const void* xv, void* 
     // every FFT line (and the 5 basis lines of a z pencil) must fit one block's register staging
     if (Px > MAXPTS * NTHR || Py > MAXPTS * NTHR || 5 * Pz > MAXPTS * NTHR)
         return set_err(h, SVH_ERR_ARG, "svh_matvec: FFT size above the per-block limit of this build");
-    const size_t b1 = (size_t)nb * 5 * nza * h->Ky * Px * csz;
-    const size_t b2 = (size_t)nb * 5 * nza * (size_t)Py * Px * csz;
-    if (h->d_B1.bytes < b1) { int rc = dev_alloc(h, h->d_B1, b1); if (rc) return rc; }
-    if (h->d_B2.bytes < b2) { int rc = dev_alloc(h, h->d_B2, b2); if (rc) return rc; }
-    C* B1 = static_cast<C*>(h->d_B1.p);
-    C* B2 = static_cast<C*>(h->d_B2.p);
+    C* B1 = static_cast<C*>(B1v);
+    C* B2 = static_cast<C*>(B2v);
     const int ti = std::is_same<T, float>::value ? 0 : 1;
     const C* twx = static_cast<const C*>(ti == 0 ? h->d_tw32[0].p : h->d_tw64[0].p);
     const C* twy = static_cast<const C*>(ti == 0 ? h->d_tw32[1].p : h->d_tw64[1].p);
@@ -365,7 +372,7 @@ static int launch_matvec(Handle* h, double omega, int nb, const void* xv, void* 
 
     prof_mark(h, -1);
     // pass 3 needs the spectra: rebuild them from Tucker first when asked (Eq. 10)
-    if (ti == 0 && h->kernel_mode == SVH_KERNELS_TUCKER_REBUILD) {
+    if (allow_rebuild && ti == 0 && h->kernel_mode == SVH_KERNELS_TUCKER_REBUILD) {
         int rc = launch_tucker_rebuild(h);
         if (rc) return rc;
     }
@@ -437,11 +444,25 @@ static int launch_matvec(Handle* h, double omega, int nb, const void* xv, void* 
     return SVH_OK;
 }
 
+// The library-allocated path: grows the handle's intermediate grids when needed.
+template <typename T>
+static int launch_matvec(Handle* h, double omega, int nb, const void* xv, void* yv, int masked) {
+    size_t b1, b2;
+    matvec_scratch_bytes(h, nb, std::is_same<T, float>::value ? SVH_FP32 : SVH_FP64, &b1, &b2);
+    if (h->d_B1.bytes < b1) { int rc = dev_alloc(h, h->d_B1, b1); if (rc) return rc; }
+    if (h->d_B2.bytes < b2) { int rc = dev_alloc(h, h->d_B2, b2); if (rc) return rc; }
+    return run_matvec<T>(h, omega, nb, xv, yv, masked, h->d_B1.p, h->d_B2.p, true);
+}
+
 int launch_matvec32(Handle* h, double omega, int nb, const void* x, void* y, int masked) {
     return launch_matvec<float>(h, omega, nb, x, y, masked);
 }
 int launch_matvec64(Handle* h, double omega, int nb, const void* x, void* y, int masked) {
     return launch_matvec<double>(h, omega, nb, x, y, masked);
+}
+int launch_matvec_on(Handle* h, double omega, int nb, const void* x, void* y, int precision, void* B1, void* B2) {
+    return precision == SVH_FP32 ? run_matvec<float>(h, omega, nb, x, y, 0, B1, B2, false)
+                                 : run_matvec<double>(h, omega, nb, x, y, 0, B1, B2, false);
 }
 
 }  // namespace svh

@@ -89,6 +89,9 @@ int dev_upload(Handle* h, DevBuf& b, const void* src, size_t bytes);
 // launchers (matvec.cu)
 int launch_matvec32(Handle* h, double omega, int nb, const void* x, void* y, int masked);
 int launch_matvec64(Handle* h, double omega, int nb, const void* x, void* y, int masked);
+// same product on caller-provided intermediate grids (no allocation, no Tucker restore)
+int launch_matvec_on(Handle* h, double omega, int nb, const void* x, void* y, int precision, void* B1, void* B2);
+void matvec_scratch_bytes(const Handle* h, int nb, int precision, size_t* b1, size_t* b2);
 // quadrature of the unit kernels (kernels_gen.cu): fills T[7][Kz][Ky][Kx] (host)
 int generate_toeplitz_device(Handle* h, std::vector<double>& T);
 // Tucker rebuild (tucker.cu)

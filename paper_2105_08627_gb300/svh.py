@@ -80,6 +80,7 @@ SIGNATURES = {
     "svh_rebuild_spectra": (C.c_int, [_P]),
     "svh_matvec": (C.c_int, [_P, C.c_double, C.c_int, _P, _P, C.c_int]),
     "svh_matvec_host": (C.c_int, [_P, C.c_double, C.c_int, _P, _P, C.c_int]),
+    "svh_matvec_noalloc": (C.c_int, [_P, C.c_double, C.c_int, _P, _P, C.c_int]),
     "svh_profile_begin": (C.c_int, [_P, C.c_int]),
     "svh_profile_end": (C.c_int, [_P, _DP, _I32P]),
     "svh_host_face_nodes": (C.c_int, [C.c_int, C.c_int, C.c_int, _U8P, _I64P, _I64P, _I32P]),
@@ -294,6 +295,11 @@ class Handle:
             y = torch.empty_like(x)
         self.matvec_ptr(omega, nb, x.data_ptr(), y.data_ptr(), prec)
         return y
+
+    def matvec_noalloc_ptr(self, omega, nb, x_ptr, y_ptr, precision):
+        """svh_matvec_noalloc: the product on the library's fixed 64 MiB device scratch (no allocation)."""
+        self._ck(lib().svh_matvec_noalloc(self._h, float(omega), int(nb), _P(x_ptr), _P(y_ptr), int(precision)),
+                 "svh_matvec_noalloc")
 
     PASSES = ("tucker_rebuild", "x_fwd", "y_fwd", "z_pass", "y_inv", "x_inv_epilogue", "node_rows")
 
