@@ -1,0 +1,370 @@
+// fastpass.cuh -- size-specialised FFT passes of the operator product (Eq. 9).
+//
+// x and y passes use the four-step split N = N1 * N2 (N1 >= N2, both <= 32):
+//   step 1: each thread loads the N1 points n1*N2 + n2 (n2 fixed) straight
+//           from HBM, takes a register DFT of length N1, multiplies by
+//           w_N^(n2 k1) and parks the result in shared memory;
+//   step 3: each thread gathers the N2 points (n2, k1) of one k1, takes a
+//           register DFT of length N2 and writes X[k1 + N1 k2] straight to HBM.
+// Lines contiguous in HBM (x) map n2 / k1 to consecutive threads; strided
+// lines (y) map the contiguous kx column index to consecutive threads. So
+// every HBM access is a coalesced row segment and each point crosses shared
+// memory once. The z pass keeps one whole Pz-point line per thread.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fft_reg.cuh"
+
+namespace svh {
+
+// Everything a pass kernel reads, passed by value.
+struct PassArgs {
+    const void* x;           // input vectors, nb * Nvec complex
+    void* y;                 // output vectors
+    void* B1;                // [nb*5][nza][Ky][Px]
+    void* B2;                // [nb*5][nza][Py][Px]
+    const void* spec;        // octant spectra [7][Hz][Hy][Hx] (float or double)
+    const void* twx;         // exp(-2 pi i m / Px), m < Px
+    const void* twy;
+    const void* twz;
+    const int32_t* vidx;     // [nza][Ky][Kx] voxel index or -1
+    const int32_t* rows;     // active rows zi*Ky + y
+    const uint8_t* rowmask;  // [nza][Ky]
+    const int32_t* zlist;    // active planes
+    const int32_t* node;     // [K][6]
+    const uint8_t* freem;    // [M]
+    const double* lam;
+    const double* sig0;
+    int64_t K, M, Nvec;
+    int64_t nlines;          // nb * 5 * nrows
+    int nb, nza, nrows, Kx, Ky, Kz, Px, Py, Pz, Hx, Hy, Hz;
+    double omega, mu, dx, conv_scale;
+    int masked;
+};
+
+// outward flux of basis alpha through face f (-x,+x,-y,+y,-z,+z)
+__device__ __forceinline__ float face_flux(int a, int f) {
+    // x: -1,+1 on x faces; y: on y faces; z: on z faces; 2D: +1/2 on x, -1/2 on y;
+    // 3D: +1/2 on x and y faces, -1 on z faces
+    const int ax = f >> 1;
+    const float sgn = (f & 1) ? 1.f : -1.f;
+    switch (a) {
+        case 0: return ax == 0 ? sgn : 0.f;
+        case 1: return ax == 1 ? sgn : 0.f;
+        case 2: return ax == 2 ? sgn : 0.f;
+        case 3: return ax == 0 ? 0.5f : (ax == 1 ? -0.5f : 0.f);
+        default: return ax == 2 ? -1.f : 0.5f;
+    }
+}
+
+// y^beta = j conv_scale conv + z^beta I^beta - (A^T Phi)^beta for voxel vi, item b (Eq. 7, 9, 16-18, 22-23)
+template <typename T>
+__device__ __forceinline__ typename CT<T>::type epilogue(const PassArgs& a, int64_t b, int be, int vi,
+                                                         typename CT<T>::type cv) {
+    using C = typename CT<T>::type;
+    const C* xb = static_cast<const C*>(a.x) + b * a.Nvec;
+    C val;
+    val.x = -(T)a.conv_scale * cv.y;
+    val.y = (T)a.conv_scale * cv.x;
+    // two-fluid c = a + j omega mu b (Eq. 22-23), z^beta = c s_beta / dx
+    const T lm = (T)a.lam[vi], s0 = (T)a.sig0[vi];
+    const T wml2 = (T)(a.omega * a.mu) * lm * lm;
+    const T tt = s0 * wml2;
+    const T den = (T)1 + tt * tt;
+    const T sb = be < 3 ? (T)1 : (be == 3 ? (T)(1.0 / 6.0) : (T)0.5);
+    const T sc = sb / (T)a.dx;
+    const T zr = s0 * wml2 * wml2 / den * sc;
+    const T zi = (T)(a.omega * a.mu) * (lm * lm / den) * sc;
+    const C I = xb[be * a.K + vi];
+    val.x += zr * I.x - zi * I.y;
+    val.y += zr * I.y + zi * I.x;
+    const int32_t* nd = a.node + (int64_t)vi * 6;
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+        const float fl = face_flux(be, f);
+        if (fl != 0.f) {
+            const int m = nd[f];
+            if (!a.masked || a.freem[m]) {
+                const C ph = xb[5 * a.K + m];
+                val.x -= (T)fl * ph.x;
+                val.y -= (T)fl * ph.y;
+            }
+        }
+    }
+    return val;
+}
+
+// ---------------------------------------------------------------- x passes (contiguous lines)
+// INV = false: gather I^alpha from the voxel list, forward FFT, write B1 rows.
+// INV = true : read B1 rows, inverse FFT, keep x < Kx, epilogue to y.
+template <typename T, int N1, int N2, bool INV, int NT>
+__global__ void __launch_bounds__(NT) k_xrow(const __grid_constant__ PassArgs a) {
+    using C = typename CT<T>::type;
+    constexpr int N = N1 * N2;
+    constexpr int L = NT / N2;            // lines per block
+    constexpr int LDS = N1 + 1;           // padded stride of n2 rows in shared memory
+    constexpr int TPT = (L * N1 + NT - 1) / NT;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* tw = reinterpret_cast<C*>(smem_raw);
+    C* buf = tw + N;
+    const C* twg = static_cast<const C*>(a.twx);
+    for (int i = threadIdx.x; i < N; i += NT) tw[i] = twg[i];
+    const int64_t line0 = (int64_t)blockIdx.x * L;
+    {
+        const int l = threadIdx.x / N2, n2 = threadIdx.x % N2;
+        const int64_t line = line0 + l;
+        C v[N1];
+        if (line < a.nlines) {
+            const int64_t ba = line / a.nrows;
+            const int row = a.rows[line - ba * a.nrows];
+            if (!INV) {
+                const int64_t b = ba / 5;
+                const int al = (int)(ba - 5 * b);
+                const C* xb = static_cast<const C*>(a.x) + b * a.Nvec + al * a.K;
+                const int32_t* vr = a.vidx + (int64_t)row * a.Kx;
+#pragma unroll
+                for (int n1 = 0; n1 < N1; ++n1) {
+                    const int n = n1 * N2 + n2;
+                    C z; z.x = 0; z.y = 0;
+                    if (n < a.Kx) {
+                        const int vi = __ldg(vr + n);
+                        if (vi >= 0) z = xb[vi];
+                    }
+                    v[n1] = z;
+                }
+            } else {
+                const C* src = static_cast<const C*>(a.B1) + (ba * a.nza * a.Ky + row) * (int64_t)N;
+#pragma unroll
+                for (int n1 = 0; n1 < N1; ++n1) v[n1] = src[n1 * N2 + n2];
+            }
+        } else {
+#pragma unroll
+            for (int n1 = 0; n1 < N1; ++n1) { v[n1].x = 0; v[n1].y = 0; }
+        }
+        reg_fft<N1, INV>(v);
+        __syncthreads();   // twiddle table ready
+#pragma unroll
+        for (int k1 = 1; k1 < N1; ++k1) {
+            const int m = (n2 * k1) % N;
+            if (m) v[k1] = INV ? cmulc(v[k1], tw[m]) : cmul(v[k1], tw[m]);
+        }
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) buf[(l * N2 + n2) * LDS + k1] = v[k1];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < TPT; ++it) {
+        const int task = threadIdx.x + it * NT;
+        if (task >= L * N1) break;
+        const int l = task / N1, k1 = task % N1;
+        const int64_t line = line0 + l;
+        if (line >= a.nlines) continue;
+        C u[N2];
+#pragma unroll
+        for (int n2 = 0; n2 < N2; ++n2) u[n2] = buf[(l * N2 + n2) * LDS + k1];
+        reg_fft<N2, INV>(u);
+        const int64_t ba = line / a.nrows;
+        const int row = a.rows[line - ba * a.nrows];
+        if (!INV) {
+            C* dst = static_cast<C*>(a.B1) + (ba * a.nza * a.Ky + row) * (int64_t)N;
+#pragma unroll
+            for (int k2 = 0; k2 < N2; ++k2) dst[k1 + N1 * k2] = u[k2];
+        } else {
+            const int64_t b = ba / 5;
+            const int be = (int)(ba - 5 * b);
+            const int32_t* vr = a.vidx + (int64_t)row * a.Kx;
+            C* yb = static_cast<C*>(a.y) + b * a.Nvec + be * a.K;
+#pragma unroll
+            for (int k2 = 0; k2 < N2; ++k2) {
+                const int k = k1 + N1 * k2;
+                if (k < a.Kx) {
+                    const int vi = __ldg(vr + k);
+                    if (vi >= 0) yb[vi] = epilogue<T>(a, b, be, vi, u[k2]);
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- y passes (strided lines, kx tiles)
+// INV = false: B1 rows y < Ky (active) -> forward FFT -> B2 rows ky < Py.
+// INV = true : B2 -> inverse FFT -> B1 active rows y < Ky.
+template <typename T, int N1, int N2, bool INV, int NT>
+__global__ void __launch_bounds__(NT) k_ycol_fast(const __grid_constant__ PassArgs a) {
+    using C = typename CT<T>::type;
+    constexpr int N = N1 * N2;
+    constexpr int TB = NT / N2;           // kx columns per block
+    constexpr int TPT = (TB * N1 + NT - 1) / NT;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* tw = reinterpret_cast<C*>(smem_raw);
+    C* buf = tw + N;                      // [n2][k1][TB]
+    const C* twg = static_cast<const C*>(a.twy);
+    for (int i = threadIdx.x; i < N; i += NT) tw[i] = twg[i];
+    const int kx0 = blockIdx.x * TB;
+    const int zi = blockIdx.y;
+    const int64_t ba = blockIdx.z;
+    const int Px = a.Px;
+    const uint8_t* rm = a.rowmask + (int64_t)zi * a.Ky;
+    {
+        const int c = threadIdx.x % TB, n2 = threadIdx.x / TB;
+        const bool colok = kx0 + c < Px;
+        C v[N1];
+        if (!INV) {
+            const C* src = static_cast<const C*>(a.B1) + ((ba * a.nza + zi) * (int64_t)a.Ky) * Px + kx0 + c;
+#pragma unroll
+            for (int n1 = 0; n1 < N1; ++n1) {
+                const int n = n1 * N2 + n2;
+                C z; z.x = 0; z.y = 0;
+                if (colok && n < a.Ky && rm[n]) z = src[(int64_t)n * Px];
+                v[n1] = z;
+            }
+        } else {
+            const C* src = static_cast<const C*>(a.B2) + ((ba * a.nza + zi) * (int64_t)N) * Px + kx0 + c;
+#pragma unroll
+            for (int n1 = 0; n1 < N1; ++n1) {
+                C z; z.x = 0; z.y = 0;
+                if (colok) z = src[(int64_t)(n1 * N2 + n2) * Px];
+                v[n1] = z;
+            }
+        }
+        reg_fft<N1, INV>(v);
+        __syncthreads();
+#pragma unroll
+        for (int k1 = 1; k1 < N1; ++k1) {
+            const int m = (n2 * k1) % N;
+            if (m) v[k1] = INV ? cmulc(v[k1], tw[m]) : cmul(v[k1], tw[m]);
+        }
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) buf[(n2 * N1 + k1) * TB + c] = v[k1];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < TPT; ++it) {
+        const int task = threadIdx.x + it * NT;
+        if (task >= TB * N1) break;
+        const int c = task % TB, k1 = task / TB;
+        if (kx0 + c >= Px) continue;
+        C u[N2];
+#pragma unroll
+        for (int n2 = 0; n2 < N2; ++n2) u[n2] = buf[(n2 * N1 + k1) * TB + c];
+        reg_fft<N2, INV>(u);
+        if (!INV) {
+            C* dst = static_cast<C*>(a.B2) + ((ba * a.nza + zi) * (int64_t)N) * Px + kx0 + c;
+#pragma unroll
+            for (int k2 = 0; k2 < N2; ++k2) dst[(int64_t)(k1 + N1 * k2) * Px] = u[k2];
+        } else {
+            C* dst = static_cast<C*>(a.B1) + ((ba * a.nza + zi) * (int64_t)a.Ky) * Px + kx0 + c;
+#pragma unroll
+            for (int k2 = 0; k2 < N2; ++k2) {
+                const int k = k1 + N1 * k2;
+                if (k < a.Ky && rm[k]) dst[(int64_t)k * Px] = u[k2];
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- z pass (whole pencils per thread)
+// Block: 5 warps (warp = basis alpha), lane = kx offset in a 32-wide tile, one ky.
+template <typename T>
+__device__ __forceinline__ void block_multiply5(typename CT<T>::type* io, T g, T sx, T sy, T sz, T qx, T qy, T qz) {
+    using C = typename CT<T>::type;
+    // the S-kernel spectra are -i*sign*R: mi(a) = -i a, pi(a) = +i a
+    auto mi = [](C v) { C c; c.x = v.y; c.y = -v.x; return c; };
+    auto pi = [](C v) { C c; c.x = -v.y; c.y = v.x; return c; };
+    C Ix = io[0], Iy = io[1], Iz = io[2], I2 = io[3], I3 = io[4];
+    C Yx = cadd(cscale(Ix, g), cscale(mi(cadd(I2, I3)), sx));
+    C Yy = cadd(cscale(Iy, g), cscale(mi(csub(I3, I2)), sy));
+    C Yz = cadd(cscale(Iz, g), cscale(pi(I3), (T)2 * sz));
+    C pX = pi(Ix), pY = pi(Iy), pZ = pi(Iz);
+    T qs = qx + qy, qd = qx - qy;
+    C Y2 = cadd(cadd(cscale(pX, sx), cscale(pY, -sy)), cadd(cscale(I2, qs), cscale(I3, qd)));
+    C Y3 = cadd(cadd(cscale(pX, sx), cscale(pY, sy)),
+                cadd(cscale(pZ, (T)-2 * sz), cadd(cscale(I2, qd), cscale(I3, qs + (T)4 * qz))));
+    io[0] = Yx; io[1] = Yy; io[2] = Yz; io[3] = Y2; io[4] = Y3;
+}
+
+// The block's spectra (7 values at each of its PZ x 32 points) are loaded once
+// into shared memory and reused for every batch item the block loops over.
+template <typename T, int PZ>
+__global__ void __launch_bounds__(160) k_zpass_fast(const __grid_constant__ PassArgs a) {
+    using C = typename CT<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C(*buf)[PZ][32] = reinterpret_cast<C(*)[PZ][32]>(smem_raw);            // [5][PZ][32]
+    T(*sp)[PZ][32] = reinterpret_cast<T(*)[PZ][32]>(smem_raw + sizeof(C) * 5 * PZ * 32);  // [7][PZ][32]
+    const int al = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int kx0 = blockIdx.x * 32;
+    const int ky = blockIdx.y;
+    const int kx = kx0 + lane;
+    const bool ok = kx < a.Px;
+    const int Px = a.Px, Py = a.Py;
+    // spectra of the tile, with the odd-kernel signs folded in
+    {
+        const T* spec = static_cast<const T*>(a.spec);
+        const int64_t Sk = (int64_t)a.Hx * a.Hy * a.Hz;
+        const int ay = min(ky, Py - ky);
+        const T sgy = (2 * ky <= Py) ? (T)1 : (T)-1;
+        for (int task = threadIdx.x; task < PZ * 32; task += 160) {
+            const int kz = task >> 5, ln = task & 31;
+            const int kxx = min(kx0 + ln, Px - 1);
+            const int ax = min(kxx, Px - kxx), az = min(kz, PZ - kz);
+            const T sgx = (2 * kxx <= Px) ? (T)1 : (T)-1;
+            const T sgz = (2 * kz <= PZ) ? (T)1 : (T)-1;
+            const int64_t off = ((int64_t)az * a.Hy + ay) * a.Hx + ax;
+            sp[0][kz][ln] = __ldg(spec + off);
+            sp[1][kz][ln] = sgx * __ldg(spec + Sk + off);
+            sp[2][kz][ln] = sgy * __ldg(spec + 2 * Sk + off);
+            sp[3][kz][ln] = sgz * __ldg(spec + 3 * Sk + off);
+            sp[4][kz][ln] = __ldg(spec + 4 * Sk + off);
+            sp[5][kz][ln] = __ldg(spec + 5 * Sk + off);
+            sp[6][kz][ln] = __ldg(spec + 6 * Sk + off);
+        }
+    }
+    C* B2 = static_cast<C*>(a.B2);
+    const int64_t plane = (int64_t)Py * Px;
+    C v[PZ];
+    for (int b = 0; b < a.nb; ++b) {
+        __syncthreads();   // previous item done with buf (and spectra ready)
+#pragma unroll
+        for (int z = 0; z < PZ; ++z) { v[z].x = 0; v[z].y = 0; }
+        const int64_t base = ((int64_t)(b * 5 + al) * a.nza * Py + ky) * Px + kx;
+        if (ok) {
+            // planes holding voxels go to their z slot; the rest stays zero
+#pragma unroll
+            for (int z = 0; z < PZ; ++z) buf[al][z][lane] = v[z];
+            for (int zi = 0; zi < a.nza; ++zi) buf[al][a.zlist[zi]][lane] = B2[base + zi * plane];
+#pragma unroll
+            for (int z = 0; z < PZ; ++z) v[z] = buf[al][z][lane];
+        }
+        reg_fft<PZ, false>(v);
+#pragma unroll
+        for (int z = 0; z < PZ; ++z) buf[al][z][lane] = v[z];
+        __syncthreads();
+        for (int task = threadIdx.x; task < PZ * 32; task += 160) {
+            const int kz = task >> 5, ln = task & 31;
+            C io[5];
+#pragma unroll
+            for (int q = 0; q < 5; ++q) io[q] = buf[q][kz][ln];
+            block_multiply5<T>(io, sp[0][kz][ln], sp[1][kz][ln], sp[2][kz][ln], sp[3][kz][ln], sp[4][kz][ln],
+                               sp[5][kz][ln], sp[6][kz][ln]);
+#pragma unroll
+            for (int q = 0; q < 5; ++q) buf[q][kz][ln] = io[q];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int z = 0; z < PZ; ++z) v[z] = buf[al][z][lane];
+        reg_fft<PZ, true>(v);
+        if (ok) {
+#pragma unroll
+            for (int z = 0; z < PZ; ++z) buf[al][z][lane] = v[z];   // own column only
+            for (int zi = 0; zi < a.nza; ++zi) B2[base + zi * plane] = buf[al][a.zlist[zi]][lane];
+        }
+    }
+}
+
+// launchers (return false when the size has no specialised kernel)
+template <typename T> bool launch_x_fast(const PassArgs& a, bool inv, cudaStream_t s);
+template <typename T> bool launch_y_fast(const PassArgs& a, bool inv, cudaStream_t s);
+template <typename T> bool launch_z_fast(const PassArgs& a, cudaStream_t s);
+
+}  // namespace svh

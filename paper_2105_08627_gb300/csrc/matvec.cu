@@ -20,6 +20,7 @@
 #include <algorithm>
 #include <cstdio>
 
+#include "fastpass.cuh"
 #include "fft.cuh"
 #include "svh_internal.h"
 
@@ -369,6 +370,22 @@ static int run_matvec(Handle* h, double omega, int nb, const void* xv, void* yv,
     const int32_t* vidx = static_cast<const int32_t*>(h->d_vidx.p);
     const int32_t* rows = static_cast<const int32_t*>(h->d_rows.p);
     const uint8_t* d_rowmask = static_cast<const uint8_t*>(h->d_rowmask.p);
+    const double mu0 = 4e-7 * 3.14159265358979323846;
+    PassArgs pa{};
+    pa.x = x; pa.y = y; pa.B1 = B1; pa.B2 = B2; pa.spec = spec;
+    pa.twx = twx; pa.twy = twy; pa.twz = twz;
+    pa.vidx = vidx; pa.rows = rows; pa.rowmask = d_rowmask;
+    pa.zlist = static_cast<const int32_t*>(h->d_zlist.p);
+    pa.node = static_cast<const int32_t*>(h->d_node.p);
+    pa.freem = static_cast<const uint8_t*>(h->d_free.p);
+    pa.lam = static_cast<const double*>(h->d_lam.p);
+    pa.sig0 = static_cast<const double*>(h->d_sig0.p);
+    pa.K = K; pa.M = M; pa.Nvec = Nvec; pa.nlines = (int64_t)nb * 5 * nrows;
+    pa.nb = nb; pa.nza = nza; pa.nrows = nrows; pa.Kx = h->Kx; pa.Ky = h->Ky; pa.Kz = h->Kz;
+    pa.Px = Px; pa.Py = Py; pa.Pz = Pz; pa.Hx = h->Hx; pa.Hy = h->Hy; pa.Hz = h->Hz;
+    pa.omega = omega; pa.mu = mu0; pa.dx = h->dx;
+    pa.conv_scale = omega * mu0 * h->dx / ((double)Px * Py * Pz);
+    pa.masked = masked;
 
     prof_mark(h, -1);
     // pass 3 needs the spectra: rebuild them from Tucker first when asked (Eq. 10)
@@ -378,7 +395,7 @@ static int run_matvec(Handle* h, double omega, int nb, const void* xv, void* yv,
     }
     prof_mark(h, 0);
     // pass 1
-    {
+    if (!launch_x_fast<T>(pa, false, h->stream)) {
         int lpb = std::max(1, MAXPTS * NTHR / Px);
         int64_t nlines = (int64_t)nb * 5 * nrows;
         size_t sm = (size_t)(Px + lpb * (Px + 1)) * csz;
@@ -390,7 +407,7 @@ static int run_matvec(Handle* h, double omega, int nb, const void* xv, void* yv,
     prof_mark(h, 1);
     // pass 2
     int tby = std::max(1, std::min(32, MAXPTS * NTHR / Py));
-    {
+    if (!launch_y_fast<T>(pa, false, h->stream)) {
         size_t sm = (size_t)(Py + Py * tby) * csz;
         cudaFuncSetAttribute(k_ycol<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         dim3 grid((Px + tby - 1) / tby, nza, nb * 5);
@@ -398,7 +415,7 @@ static int run_matvec(Handle* h, double omega, int nb, const void* xv, void* yv,
     }
     prof_mark(h, 2);
     // pass 3
-    {
+    if (!launch_z_fast<T>(pa, h->stream)) {
         int tbz = std::max(1, std::min(64, MAXPTS * NTHR / (5 * Pz)));
         size_t sm = (size_t)(Pz + Pz * 5 * tbz) * csz;
         cudaFuncSetAttribute(k_zpass<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -408,7 +425,7 @@ static int run_matvec(Handle* h, double omega, int nb, const void* xv, void* yv,
     }
     prof_mark(h, 3);
     // pass 4
-    {
+    if (!launch_y_fast<T>(pa, true, h->stream)) {
         size_t sm = (size_t)(Py + Py * tby) * csz;
         cudaFuncSetAttribute(k_ycol<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         dim3 grid((Px + tby - 1) / tby, nza, nb * 5);
@@ -416,7 +433,7 @@ static int run_matvec(Handle* h, double omega, int nb, const void* xv, void* yv,
     }
     prof_mark(h, 4);
     // pass 5 + epilogue
-    {
+    if (!launch_x_fast<T>(pa, true, h->stream)) {
         int lpb = std::max(1, MAXPTS * NTHR / Px);
         int64_t nlines = (int64_t)nb * 5 * nrows;
         size_t sm = (size_t)(Px + lpb * (Px + 1)) * csz;

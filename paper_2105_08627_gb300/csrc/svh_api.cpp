@@ -104,6 +104,8 @@ static void free_kernels(Handle* h) {
     }
     dev_free(h->d_tk_w1);
     dev_free(h->d_tk_w2);
+    dev_free(h->d_tk_probs);
+    ++h->tk_version;
     h->have_kernels = false;
     h->toep.clear();
     h->spec.clear();
@@ -455,6 +457,7 @@ static int upload_tucker(Handle* h, int u) {
         if (rc) return rc;
     }
     h->tucker_on[u] = true;
+    ++h->tk_version;
     return SVH_OK;
 }
 

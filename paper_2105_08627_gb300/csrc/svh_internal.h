@@ -66,6 +66,10 @@ struct Handle {
     Tucker tk[7];
     DevBuf d_tk_core[7], d_tk_F[7][3];   // float
     DevBuf d_tk_w1, d_tk_w2;             // rebuild intermediates (float)
+    DevBuf d_tk_probs;                   // GEMM descriptors of the restore
+    std::vector<char> tk_probs;          // host copy of the descriptors
+    int tk_probs_split[3] = {0, 0, 0};
+    int tk_version = 0, tk_probs_version = -1;
     int kernel_mode = SVH_KERNELS_RESIDENT;
 
     // ---- per-pass profiling (svh_profile_begin/end)
