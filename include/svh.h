@@ -164,6 +164,54 @@ int svh_matvec(svh_handle* h, double omega, int nb, const void* x_dev, void* y_d
 int svh_matvec_host(svh_handle* h, double omega, int nb, const void* x, void* y,
                     int precision);
 
+/* ---- Port solves (Sec. II.C and Sec. III).
+ * For each angular frequency and each port j, solves Eq. 7 with a unit
+ * potential on port j's plus-terminal nodes and zero on every other fixed
+ * node (all ports' terminals and one gauge node per floating island); fixed
+ * nodes leave the unknowns. The solver is right-preconditioned flexible
+ * GMRES(restart) with FP64 Arnoldi on the device; the preconditioner is the
+ * sparse P = Q^{-1}, Q = [Y, -A^T; A, 0], Y = diag(|Z_kk|) (Eq. 12), applied
+ * through the Schur complement S = A Y^{-1} A^T (Eq. 13-15) whose solves run
+ * on the host by AMG-preconditioned CG to amg_tol. With inner_precision =
+ * SVH_FP32 the Krylov products use the FP32 operator and an FP64 refinement
+ * loop restores the FP64 residual. The iteration stops when every port's
+ * relative residual ||b - K x|| / ||b||, measured with the FP64 operator, is
+ * <= rre. Port currents I_p = sum of (A I) over port p's plus-terminal nodes
+ * give the admittance Y[p][j]; Zport = Y^{-1} (the inductance is Im(Z)/omega). */
+typedef struct {
+    int32_t restart;           /* GMRES restart length (default 50, Sec. III) */
+    int32_t max_iterations;    /* inner iterations per refinement step (default 2000) */
+    int32_t max_refinements;   /* FP64 refinement steps (default 8) */
+    int32_t inner_precision;   /* SVH_FP32 (default) or SVH_FP64 */
+    double rre;                /* relative residual target (default 1e-8, Sec. III) */
+    double amg_tol;            /* relative tolerance of each Schur solve (default 1e-8, Sec. II.C) */
+} svh_options;
+
+typedef struct {
+    int32_t iterations;        /* inner GMRES iterations, all frequencies */
+    int32_t refinements;       /* refinement steps, all frequencies */
+    int32_t amg_levels;        /* levels of the last AMG hierarchy */
+    double amg_avg_iterations; /* CG iterations per Schur solve, last frequency */
+    double final_rre;          /* largest final relative residual over ports and frequencies */
+    double setup_seconds;      /* preconditioner set-up time */
+    double solve_seconds;      /* everything else */
+} svh_stats;
+
+void svh_default_options(svh_options* opt);
+/* omegas[nfreq] (rad/s, > 0); Zport receives nfreq * nports * nports complex
+ * values (interleaved), Zport[f][p][q]. opt may be NULL (defaults), st may be
+ * NULL. Returns SVH_ERR_NOT_CONVERGED (with Zport filled) if some residual
+ * stays above rre. Requires kernels and at least one port. */
+int svh_solve(svh_handle* h, const double* omegas, int nfreq, const svh_options* opt, double* Zport,
+              svh_stats* st);
+/* Solution vector x[N] (complex interleaved double) of port `port` at the
+ * last frequency of the last svh_solve (fixed-node potentials are 0). */
+int svh_get_solution(const svh_handle* h, int port, double* x);
+/* Host reference of the preconditioner apply out = P in (Eq. 13-15) at
+ * omega for nb vectors of length N (complex interleaved double), with the
+ * Schur solves run to 1e-12 (for tests). */
+int svh_precond_apply(svh_handle* h, double omega, int nb, const double* in, double* out);
+
 /* ---- Product for callers that cannot allocate device memory at call time.
  * (An interface of this library; the paper has no counterpart.)
  * svh_matvec allocates its intermediate FFT grids with cudaMalloc the first
@@ -208,6 +256,14 @@ int svh_host_face_nodes(int Kx, int Ky, int Kz, const uint8_t* occ, int64_t* K_o
 /* Octant spectra S[7][Pz/2+1][Py/2+1][Px/2+1] of the circulant embeddings of
  * unit kernels T[7][Kz][Ky][Kx] (same definition as svh_get_spectra). */
 int svh_host_spectra(int Kx, int Ky, int Kz, int Px, int Py, int Pz, const double* T, double* S);
+/* S x = b for a real symmetric positive definite CSR matrix (rowptr[n+1],
+ * colidx, vals) by conjugate gradients preconditioned with the library's
+ * aggregation AMG V-cycle (the inner solver of the Schur complement, Eq. 14),
+ * x0 = 0, to ||b - S x|| <= tol ||b||. iters, levels (may be NULL) receive the
+ * CG iterations and the number of AMG levels. SVH_ERR_NOT_CONVERGED after
+ * maxit iterations; SVH_ERR_SINGULAR if the coarsest level is not SPD. */
+int svh_host_amg_solve(int n, const int32_t* rowptr, const int32_t* colidx, const double* vals, const double* b,
+                       double* x, double tol, int maxit, int32_t* iters, int32_t* levels);
 /* Algorithm 1 (Tucker-SVD) of a real D1 x D2 x D3 array O stored with the
  * mode-1 index fastest, O[(i3*D2 + i2)*D1 + i1]. The rank of mode i is the
  * smallest d_i whose discarded singular values have 2-norm <= tol/sqrt(3) *

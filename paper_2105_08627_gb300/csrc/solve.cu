@@ -1,0 +1,632 @@
+// solve.cu -- port solves of Eq. 7: flexible GMRES(restart) with FP64 Arnoldi on the
+// device, the Schur-complement preconditioner of Eq. 12-15, FP32 inner products
+// with FP64 iterative refinement, and the port admittance -> impedance reduction.
+//
+// Excitation: for port j the plus-terminal nodes get Phi = 1 and every other
+// fixed node (terminals of all ports, gauge nodes of floating islands) Phi = 0.
+// Fixed nodes leave the unknowns; the library keeps the vector length N and
+// solves the masked operator Kt = D K D + (I - D) (D zeroes fixed-node
+// potentials and continuity rows) with right-hand side [A_T^T Phi_T; 0], so
+// fixed-node entries of the solution are 0. Port current I_p = sum over the
+// plus nodes of port p of (A I)_m; Y[p][j] = I_p under excitation j;
+// Z_port = Y^{-1}.
+//
+// Right preconditioning with P applied exactly as Eq. 13-15, S^{-1} by the
+// host AMG; because the AMG inner solve stops at a tolerance, the outer method
+// is flexible GMRES (the preconditioned vectors Z_k are kept). Arnoldi uses
+// classical Gram-Schmidt applied twice (CGS2) in FP64: each pass is one
+// batched dot-product kernel over the basis and one linear-combination kernel.
+// Givens rotations and the small least-squares solves run on the host.
+// Refinement: r = b - Kt x in FP64, inner FGMRES on Kt (FP32 products) to a
+// relative reduction of 1e-5 (or to the target), x += correction, until
+// ||r|| / ||b|| <= rre measured with the FP64 product (Sec. III: RRE 1e-8).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <vector>
+
+#include "fft.cuh"
+#include "svh_internal.h"
+
+namespace svh {
+
+using cdbl = std::complex<double>;
+
+static const double kFluxH[5][6] = {
+    {-1, 1, 0, 0, 0, 0}, {0, 0, -1, 1, 0, 0}, {0, 0, 0, 0, -1, 1}, {0.5, 0.5, -0.5, -0.5, 0, 0}, {0.5, 0.5, 0.5, 0.5, -1, -1}};
+__constant__ double c_fluxd[5][6] = {
+    {-1, 1, 0, 0, 0, 0}, {0, 0, -1, 1, 0, 0}, {0, 0, 0, 0, -1, 1}, {0.5, 0.5, -0.5, -0.5, 0, 0}, {0.5, 0.5, 0.5, 0.5, -1, -1}};
+
+constexpr int DOT_THREADS = 256;
+constexpr int DOT_PER_THREAD = 8;
+
+// partial[r][blk][i] = sum over the block's slice of conj(V[r][i][n]) * w[r][n], i < nv
+__global__ void __launch_bounds__(DOT_THREADS) k_dots(const double2* __restrict__ V, int64_t ldv, int64_t rstride_v,
+                                                      const double2* __restrict__ w, int64_t rstride_w, int nv,
+                                                      int64_t n, double2* __restrict__ partial, int nblk) {
+    const int r = blockIdx.y;
+    const int64_t n0 = (int64_t)blockIdx.x * DOT_THREADS * DOT_PER_THREAD;
+    double2 wv[DOT_PER_THREAD];
+    const double2* wr = w + r * rstride_w;
+#pragma unroll
+    for (int q = 0; q < DOT_PER_THREAD; ++q) {
+        const int64_t idx = n0 + threadIdx.x + (int64_t)q * DOT_THREADS;
+        if (idx < n) wv[q] = wr[idx];
+        else { wv[q].x = 0; wv[q].y = 0; }
+    }
+    __shared__ double2 red[DOT_THREADS / 32];
+    const double2* Vr = V + r * rstride_v;
+    for (int i = 0; i < nv; ++i) {
+        const double2* vi = Vr + (int64_t)i * ldv;
+        double sr = 0, si = 0;
+#pragma unroll
+        for (int q = 0; q < DOT_PER_THREAD; ++q) {
+            const int64_t idx = n0 + threadIdx.x + (int64_t)q * DOT_THREADS;
+            if (idx < n) {
+                const double2 a = vi[idx];
+                sr += a.x * wv[q].x + a.y * wv[q].y;   // conj(a) * w
+                si += a.x * wv[q].y - a.y * wv[q].x;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            sr += __shfl_down_sync(0xffffffffu, sr, o);
+            si += __shfl_down_sync(0xffffffffu, si, o);
+        }
+        if ((threadIdx.x & 31) == 0) { red[threadIdx.x >> 5].x = sr; red[threadIdx.x >> 5].y = si; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double2 t; t.x = 0; t.y = 0;
+            for (int q = 0; q < DOT_THREADS / 32; ++q) { t.x += red[q].x; t.y += red[q].y; }
+            partial[((int64_t)r * nblk + blockIdx.x) * nv + i] = t;
+        }
+        __syncthreads();
+    }
+}
+
+// out[r][i] = sum over blocks of partial[r][blk][i]
+__global__ void k_dots_reduce(const double2* __restrict__ partial, int nblk, int nv, double2* __restrict__ out) {
+    const int r = blockIdx.y, i = blockIdx.x;
+    double sr = 0, si = 0;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
+        const double2 p = partial[((int64_t)r * nblk + b) * nv + i];
+        sr += p.x;
+        si += p.y;
+    }
+    __shared__ double s1[256], s2[256];
+    s1[threadIdx.x] = sr;
+    s2[threadIdx.x] = si;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) { s1[threadIdx.x] += s1[threadIdx.x + s]; s2[threadIdx.x] += s2[threadIdx.x + s]; }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) { out[(int64_t)r * nv + i].x = s1[0]; out[(int64_t)r * nv + i].y = s2[0]; }
+}
+
+// out[r][n] = beta * out[r][n] + sum_i coef[r][i] * V[r][i][n]
+__global__ void k_lincomb(double2* __restrict__ out, int64_t rstride_o, const double2* __restrict__ V, int64_t ldv,
+                          int64_t rstride_v, const double2* __restrict__ coef, int ldc, int nv, double beta, int64_t n) {
+    const int r = blockIdx.y;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n) return;
+    const double2* Vr = V + r * rstride_v;
+    const double2* c = coef + (int64_t)r * ldc;
+    double2 acc = out[r * rstride_o + idx];
+    acc.x *= beta;
+    acc.y *= beta;
+    for (int i = 0; i < nv; ++i) {
+        const double2 a = Vr[(int64_t)i * ldv + idx];
+        const double2 k = c[i];
+        acc.x += k.x * a.x - k.y * a.y;
+        acc.y += k.x * a.y + k.y * a.x;
+    }
+    out[r * rstride_o + idx] = acc;
+}
+
+// y[r][n] = x[r][n] * s[r] (real scale)
+__global__ void k_scale(double2* __restrict__ y, int64_t rs_y, const double2* __restrict__ x, int64_t rs_x,
+                        const double* __restrict__ s, int64_t n) {
+    const int r = blockIdx.y;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double2 v = x[r * rs_x + i];
+    v.x *= s[r];
+    v.y *= s[r];
+    y[r * rs_y + i] = v;
+}
+
+__global__ void k_to32(const double2* __restrict__ x, float2* __restrict__ y, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) { y[i].x = (float)x[i].x; y[i].y = (float)x[i].y; }
+}
+__global__ void k_to64(const float2* __restrict__ x, double2* __restrict__ y, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) { y[i].x = x[i].x; y[i].y = x[i].y; }
+}
+
+// a + b (elementwise) into a
+__global__ void k_add(double2* __restrict__ a, const double2* __restrict__ b, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) { a[i].x += b[i].x; a[i].y += b[i].y; }
+}
+
+// a - b (elementwise) into a
+__global__ void k_sub(double2* __restrict__ a, const double2* __restrict__ b, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) { a[i].x -= b[i].x; a[i].y -= b[i].y; }
+}
+
+// Preconditioner, first half (Eq. 14 right-hand side): e_m = d_m - sum over the
+// voxel faces at free node m of flux * c / Y, for every free node (compact).
+__global__ void k_prec_pre(const double2* __restrict__ v, int64_t Nvec, int64_t K, const double* __restrict__ Y,
+                           const int32_t* __restrict__ free_nodes, int nf, const int32_t* __restrict__ ninc,
+                           double2* __restrict__ e) {
+    const int r = blockIdx.y;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nf) return;
+    const double2* vr = v + (int64_t)r * Nvec;
+    const int m = free_nodes[i];
+    double2 acc = vr[5 * K + m];
+    for (int q = 0; q < 2; ++q) {
+        const int code = ninc[2 * (int64_t)m + q];
+        if (code < 0) continue;
+        const int vx = code / 6, f = code - 6 * (code / 6);
+        for (int a = 0; a < 5; ++a) {
+            const double fl = c_fluxd[a][f];
+            if (fl == 0) continue;
+            const double yi = fl / Y[a * K + vx];
+            const double2 c = vr[a * K + vx];
+            acc.x -= yi * c.x;
+            acc.y -= yi * c.y;
+        }
+    }
+    e[(int64_t)r * nf + i] = acc;
+}
+
+// Preconditioner, second half (Eq. 15): a = Y^{-1}(c + A_F^T b); potentials:
+// b on free nodes, the input value on fixed nodes (identity rows of Kt).
+__global__ void k_prec_post_vox(const double2* __restrict__ v, double2* __restrict__ out, int64_t Nvec, int64_t K,
+                                const double* __restrict__ Y, const int32_t* __restrict__ node,
+                                const int32_t* __restrict__ free_id, const double2* __restrict__ b, int nf) {
+    const int r = blockIdx.y;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 5 * K) return;
+    const int a = (int)(t / K);
+    const int64_t vx = t - a * K;
+    const double2* vr = v + (int64_t)r * Nvec;
+    double2 s = vr[t];
+    for (int f = 0; f < 6; ++f) {
+        const double fl = c_fluxd[a][f];
+        if (fl == 0) continue;
+        const int id = free_id[node[vx * 6 + f]];
+        if (id < 0) continue;
+        const double2 bb = b[(int64_t)r * nf + id];
+        s.x += fl * bb.x;
+        s.y += fl * bb.y;
+    }
+    const double yi = 1.0 / Y[t];
+    s.x *= yi;
+    s.y *= yi;
+    out[(int64_t)r * Nvec + t] = s;
+}
+
+__global__ void k_prec_post_node(const double2* __restrict__ v, double2* __restrict__ out, int64_t Nvec, int64_t K,
+                                 int64_t M, const int32_t* __restrict__ free_id, const double2* __restrict__ b, int nf) {
+    const int r = blockIdx.y;
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    const int id = free_id[m];
+    out[(int64_t)r * Nvec + 5 * K + m] = id >= 0 ? b[(int64_t)r * nf + id] : v[(int64_t)r * Nvec + 5 * K + m];
+}
+
+// ------------------------------------------------------------------ host driver
+// Krylov storage: V[i][r][n] (i <= m) and Z[i][r][n] (i < m), so basis vector i
+// of all nb right-hand sides is one contiguous nb x N block that the batched
+// preconditioner and operator product consume directly.
+struct SolveWork {
+    int nb = 0, m = 0;
+    int64_t N = 0;
+    int nf = 0;
+    DevBuf X, B, R, W, D, V, Z, T32a, T32b, part, hbuf, E, Bs, Yd, freeid, freenodes, scl;
+    ~SolveWork() {
+        for (DevBuf* b : {&X, &B, &R, &W, &D, &V, &Z, &T32a, &T32b, &part, &hbuf, &E, &Bs, &Yd, &freeid, &freenodes, &scl})
+            dev_free(*b);
+    }
+};
+
+static unsigned blocks_for(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+static int nblk_dots(int64_t N) { return (int)((N + DOT_THREADS * DOT_PER_THREAD - 1) / (DOT_THREADS * DOT_PER_THREAD)); }
+
+// h[r][i] = V_i^H w_r for i < nv (w = s.W)
+static int dots(Handle* h, SolveWork& s, const double2* Vb, int nv, const double2* w, std::vector<cdbl>& out) {
+    const int64_t N = s.N;
+    const int nblk = nblk_dots(N);
+    k_dots<<<dim3(nblk, s.nb), DOT_THREADS, 0, h->stream>>>(Vb, (int64_t)s.nb * N, N, w, N, nv, N,
+                                                            static_cast<double2*>(s.part.p), nblk);
+    k_dots_reduce<<<dim3(nv, s.nb), 256, 0, h->stream>>>(static_cast<double2*>(s.part.p), nblk, nv,
+                                                         static_cast<double2*>(s.hbuf.p));
+    out.resize((size_t)s.nb * nv);
+    SVH_CUDA_TRY(h, cudaMemcpyAsync(out.data(), s.hbuf.p, out.size() * 16, cudaMemcpyDeviceToHost, h->stream));
+    SVH_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    return SVH_OK;
+}
+
+// out_r = beta * out_r + sum_i coef[r][i] * Vb_i,r
+static int lincomb(Handle* h, SolveWork& s, double2* out, const double2* Vb, int nv, const std::vector<cdbl>& coef,
+                   double beta) {
+    SVH_CUDA_TRY(h, cudaMemcpyAsync(s.hbuf.p, coef.data(), coef.size() * 16, cudaMemcpyHostToDevice, h->stream));
+    k_lincomb<<<dim3(blocks_for(s.N), s.nb), 256, 0, h->stream>>>(out, s.N, Vb, (int64_t)s.nb * s.N, s.N,
+                                                                   static_cast<double2*>(s.hbuf.p), nv, nv, beta, s.N);
+    return SVH_OK;
+}
+
+static int norms(Handle* h, SolveWork& s, const double2* w, std::vector<double>& out) {
+    std::vector<cdbl> t;
+    const int64_t N = s.N;
+    const int nblk = nblk_dots(N);
+    k_dots<<<dim3(nblk, s.nb), DOT_THREADS, 0, h->stream>>>(w, N, N, w, N, 1, N, static_cast<double2*>(s.part.p), nblk);
+    k_dots_reduce<<<dim3(1, s.nb), 256, 0, h->stream>>>(static_cast<double2*>(s.part.p), nblk, 1,
+                                                        static_cast<double2*>(s.hbuf.p));
+    t.resize(s.nb);
+    SVH_CUDA_TRY(h, cudaMemcpyAsync(t.data(), s.hbuf.p, t.size() * 16, cudaMemcpyDeviceToHost, h->stream));
+    SVH_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    out.resize(s.nb);
+    for (int r = 0; r < s.nb; ++r) out[r] = std::sqrt(std::max(t[r].real(), 0.0));
+    return SVH_OK;
+}
+
+// out = P in (Eq. 13-15) for the nb contiguous vectors of `in`; S^{-1} on the host
+static int apply_precond(Handle* h, SolveWork& s, const double2* in, double2* out) {
+    const int64_t K = h->K, M = h->M, N = s.N;
+    const int nf = s.nf;
+    k_prec_pre<<<dim3(blocks_for(nf), s.nb), 256, 0, h->stream>>>(in, N, K, static_cast<double*>(s.Yd.p),
+                                                                     static_cast<int32_t*>(s.freenodes.p), nf,
+                                                                     static_cast<int32_t*>(h->d_ninc.p),
+                                                                     static_cast<double2*>(s.E.p));
+    std::vector<double> e((size_t)s.nb * nf * 2), b((size_t)s.nb * nf * 2);
+    SVH_CUDA_TRY(h, cudaMemcpyAsync(e.data(), s.E.p, e.size() * 8, cudaMemcpyDeviceToHost, h->stream));
+    SVH_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    int rc = precond_schur_solve(h, s.nb, e.data(), b.data());
+    if (rc) return rc;
+    SVH_CUDA_TRY(h, cudaMemcpyAsync(s.Bs.p, b.data(), b.size() * 8, cudaMemcpyHostToDevice, h->stream));
+    k_prec_post_vox<<<dim3(blocks_for(5 * K), s.nb), 256, 0, h->stream>>>(
+        in, out, N, K, static_cast<double*>(s.Yd.p), static_cast<int32_t*>(h->d_node.p),
+        static_cast<int32_t*>(s.freeid.p), static_cast<double2*>(s.Bs.p), nf);
+    k_prec_post_node<<<dim3(blocks_for(M), s.nb), 256, 0, h->stream>>>(in, out, N, K, M,
+                                                                        static_cast<int32_t*>(s.freeid.p),
+                                                                        static_cast<double2*>(s.Bs.p), nf);
+    SVH_CUDA_TRY(h, cudaGetLastError());
+    return SVH_OK;
+}
+
+// y = Kt x (masked operator): FP64 product, or FP32 product with conversions
+static int apply_op(Handle* h, SolveWork& s, double omega, const double2* x, double2* y, int prec, int masked = 1) {
+    const int64_t n = (int64_t)s.nb * s.N;
+    if (prec == SVH_FP64) return launch_matvec64(h, omega, s.nb, x, y, masked);
+    float2* a = static_cast<float2*>(s.T32a.p);
+    float2* b = static_cast<float2*>(s.T32b.p);
+    k_to32<<<blocks_for(n), 256, 0, h->stream>>>(x, a, n);
+    int rc = launch_matvec32(h, omega, s.nb, a, b, masked);
+    if (rc) return rc;
+    k_to64<<<blocks_for(n), 256, 0, h->stream>>>(b, y, n);
+    return SVH_OK;
+}
+
+static void givens(cdbl a, cdbl b, cdbl& c, cdbl& sn) {
+    if (std::abs(b) == 0) { c = 1; sn = 0; return; }
+    if (std::abs(a) == 0) { c = 0; sn = std::conj(b) / std::abs(b); return; }
+    const double t = std::hypot(std::abs(a), std::abs(b));
+    c = std::abs(a) / t;
+    sn = (a / std::abs(a)) * std::conj(b) / t;
+}
+
+// Flexible GMRES(m) for Kt D = R with right preconditioning; D in s.D.
+// Stops right-hand side r when its estimated residual is <= tol[r] * ||R_r||.
+static int fgmres(Handle* h, SolveWork& s, double omega, int prec, const std::vector<double>& tol, int maxit,
+                  int& iters_out) {
+    const int nb = s.nb, m = s.m;
+    const int64_t N = s.N, blk = (int64_t)nb * N;
+    double2* V = static_cast<double2*>(s.V.p);
+    double2* Z = static_cast<double2*>(s.Z.p);
+    double2* W = static_cast<double2*>(s.W.p);
+    double2* Dd = static_cast<double2*>(s.D.p);
+    double2* Rr = static_cast<double2*>(s.R.p);
+    SVH_CUDA_TRY(h, cudaMemsetAsync(Dd, 0, (size_t)blk * 16, h->stream));
+    std::vector<double> beta0;
+    int rc = norms(h, s, Rr, beta0);
+    if (rc) return rc;
+    // V_0 slot temporarily holds the current residual
+    SVH_CUDA_TRY(h, cudaMemcpyAsync(V, Rr, (size_t)blk * 16, cudaMemcpyDeviceToDevice, h->stream));
+    int it = 0;
+    while (true) {
+        std::vector<double> beta;
+        if ((rc = norms(h, s, V, beta))) return rc;
+        std::vector<bool> done(nb);
+        bool all = true;
+        for (int r = 0; r < nb; ++r) {
+            done[r] = beta[r] <= tol[r] * beta0[r] || beta0[r] == 0;
+            all = all && done[r];
+        }
+        if (all || it >= maxit) break;
+        std::vector<double> inv(nb);
+        for (int r = 0; r < nb; ++r) inv[r] = beta[r] > 0 ? 1.0 / beta[r] : 0.0;
+        SVH_CUDA_TRY(h, cudaMemcpyAsync(s.scl.p, inv.data(), nb * 8, cudaMemcpyHostToDevice, h->stream));
+        k_scale<<<dim3(blocks_for(N), nb), 256, 0, h->stream>>>(V, N, V, N, static_cast<double*>(s.scl.p), N);
+        std::vector<cdbl> H((size_t)nb * (m + 1) * m, 0.0), cs((size_t)nb * m), sn((size_t)nb * m),
+            g((size_t)nb * (m + 1), 0.0);
+        for (int r = 0; r < nb; ++r) g[(size_t)r * (m + 1)] = beta[r];
+        int kk = 0;
+        for (int k = 0; k < m && it < maxit; ++k) {
+            double2* Vk = V + k * blk;
+            double2* Zk = Z + k * blk;
+            if ((rc = apply_precond(h, s, Vk, Zk))) return rc;
+            if ((rc = apply_op(h, s, omega, Zk, W, prec))) return rc;
+            // classical Gram-Schmidt, twice
+            std::vector<cdbl> h1, h2;
+            if ((rc = dots(h, s, V, k + 1, W, h1))) return rc;
+            std::vector<cdbl> neg(h1.size());
+            for (size_t i = 0; i < h1.size(); ++i) neg[i] = -h1[i];
+            if ((rc = lincomb(h, s, W, V, k + 1, neg, 1.0))) return rc;
+            if ((rc = dots(h, s, V, k + 1, W, h2))) return rc;
+            for (size_t i = 0; i < h2.size(); ++i) neg[i] = -h2[i];
+            if ((rc = lincomb(h, s, W, V, k + 1, neg, 1.0))) return rc;
+            std::vector<double> hn;
+            if ((rc = norms(h, s, W, hn))) return rc;
+            for (int r = 0; r < nb; ++r) inv[r] = hn[r] > 1e-300 * std::max(1.0, beta0[r]) ? 1.0 / hn[r] : 0.0;
+            SVH_CUDA_TRY(h, cudaMemcpyAsync(s.scl.p, inv.data(), nb * 8, cudaMemcpyHostToDevice, h->stream));
+            k_scale<<<dim3(blocks_for(N), nb), 256, 0, h->stream>>>(V + (k + 1) * blk, N, W, N,
+                                                                    static_cast<double*>(s.scl.p), N);
+            ++it;
+            kk = k + 1;
+            bool allc = true;
+            for (int r = 0; r < nb; ++r) {
+                cdbl* Hr = H.data() + (size_t)r * (m + 1) * m;   // column-major: Hr[i + k*(m+1)]
+                for (int i = 0; i <= k; ++i) Hr[i + (size_t)k * (m + 1)] = h1[(size_t)r * (k + 1) + i] + h2[(size_t)r * (k + 1) + i];
+                Hr[k + 1 + (size_t)k * (m + 1)] = hn[r];
+                cdbl* csr = cs.data() + (size_t)r * m;
+                cdbl* snr = sn.data() + (size_t)r * m;
+                for (int i = 0; i < k; ++i) {
+                    const cdbl a = Hr[i + (size_t)k * (m + 1)], b = Hr[i + 1 + (size_t)k * (m + 1)];
+                    Hr[i + (size_t)k * (m + 1)] = csr[i] * a + snr[i] * b;
+                    Hr[i + 1 + (size_t)k * (m + 1)] = -std::conj(snr[i]) * a + std::conj(csr[i]) * b;
+                }
+                givens(Hr[k + (size_t)k * (m + 1)], Hr[k + 1 + (size_t)k * (m + 1)], csr[k], snr[k]);
+                const cdbl a = Hr[k + (size_t)k * (m + 1)], b = Hr[k + 1 + (size_t)k * (m + 1)];
+                Hr[k + (size_t)k * (m + 1)] = csr[k] * a + snr[k] * b;
+                Hr[k + 1 + (size_t)k * (m + 1)] = 0;
+                cdbl* gr = g.data() + (size_t)r * (m + 1);
+                gr[k + 1] = -std::conj(snr[k]) * gr[k];
+                gr[k] = csr[k] * gr[k];
+                if (!(done[r] || std::abs(gr[k + 1]) <= tol[r] * beta0[r])) allc = false;
+            }
+            if (allc) break;
+        }
+        // y from the triangular systems; D += sum_i y_i Z_i
+        std::vector<cdbl> y((size_t)nb * kk, 0.0);
+        for (int r = 0; r < nb; ++r) {
+            if (done[r]) continue;
+            const cdbl* Hr = H.data() + (size_t)r * (m + 1) * m;
+            const cdbl* gr = g.data() + (size_t)r * (m + 1);
+            cdbl* yr = y.data() + (size_t)r * kk;
+            for (int i = kk - 1; i >= 0; --i) {
+                cdbl t = gr[i];
+                for (int j = i + 1; j < kk; ++j) t -= Hr[i + (size_t)j * (m + 1)] * yr[j];
+                const cdbl d = Hr[i + (size_t)i * (m + 1)];
+                yr[i] = std::abs(d) > 0 ? t / d : 0.0;
+            }
+        }
+        if ((rc = lincomb(h, s, Dd, Z, kk, y, 1.0))) return rc;
+        // residual of the correction problem for the restart: V_0 <- R - Kt D
+        if ((rc = apply_op(h, s, omega, Dd, W, prec))) return rc;
+        SVH_CUDA_TRY(h, cudaMemcpyAsync(V, Rr, (size_t)blk * 16, cudaMemcpyDeviceToDevice, h->stream));
+        k_sub<<<blocks_for(blk), 256, 0, h->stream>>>(V, W, blk);
+    }
+    iters_out = it;
+    SVH_CUDA_TRY(h, cudaGetLastError());
+    return SVH_OK;
+}
+
+static int alloc_work(Handle* h, SolveWork& s, int nb, int m) {
+    s.nb = nb;
+    s.m = m;
+    s.N = 5 * h->K + h->M;
+    const size_t blk = (size_t)nb * s.N;
+    int rc;
+    if ((rc = dev_alloc(h, s.X, blk * 16)) || (rc = dev_alloc(h, s.B, blk * 16)) || (rc = dev_alloc(h, s.R, blk * 16)) ||
+        (rc = dev_alloc(h, s.W, blk * 16)) || (rc = dev_alloc(h, s.D, blk * 16)) ||
+        (rc = dev_alloc(h, s.V, (size_t)(m + 1) * blk * 16)) || (rc = dev_alloc(h, s.Z, (size_t)m * blk * 16)) ||
+        (rc = dev_alloc(h, s.T32a, blk * 8)) || (rc = dev_alloc(h, s.T32b, blk * 8)) ||
+        (rc = dev_alloc(h, s.part, (size_t)nblk_dots(s.N) * nb * (m + 1) * 16)) ||
+        (rc = dev_alloc(h, s.hbuf, (size_t)nb * (m + 1) * 16)) || (rc = dev_alloc(h, s.scl, (size_t)nb * 8)))
+        return rc;
+    return SVH_OK;
+}
+
+}  // namespace svh
+
+using namespace svh;
+
+extern "C" {
+
+void svh_default_options(svh_options* o) {
+    if (!o) return;
+    o->restart = 50;
+    o->max_iterations = 2000;
+    o->max_refinements = 8;
+    o->inner_precision = SVH_FP32;
+    o->rre = 1e-8;
+    o->amg_tol = 1e-8;
+}
+
+int svh_solve(svh_handle* hh, const double* omegas, int nfreq, const svh_options* opt_in, double* Zport,
+              svh_stats* st) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h) return SVH_ERR_ARG;
+    cudaError_t ce = cudaSetDevice(h->device);
+    if (ce != cudaSuccess) return cuda_err(h, ce, "cudaSetDevice");
+    if (!h->have_grid || !h->have_kernels) return set_err(h, SVH_ERR_STATE, "svh_solve: grid and kernels needed");
+    const int np = (int)h->port_plus.size();
+    if (np == 0) return set_err(h, SVH_ERR_STATE, "svh_solve: the grid has no ports");
+    if (!omegas || nfreq <= 0 || !Zport) return set_err(h, SVH_ERR_ARG, "svh_solve: bad frequencies or output");
+    svh_options opt;
+    svh_default_options(&opt);
+    if (opt_in) opt = *opt_in;
+    if (opt.restart < 1 || opt.restart > 500 || !(opt.rre > 0) || !(opt.amg_tol > 0) || opt.max_iterations < 1 ||
+        opt.max_refinements < 1 || (opt.inner_precision != SVH_FP32 && opt.inner_precision != SVH_FP64))
+        return set_err(h, SVH_ERR_ARG, "svh_solve: bad options");
+    for (int f = 0; f < nfreq; ++f)
+        if (!(omegas[f] > 0) || !std::isfinite(omegas[f])) return set_err(h, SVH_ERR_ARG, "svh_solve: omega must be > 0");
+    const auto t0 = std::chrono::steady_clock::now();
+    double setup_s = 0;
+    const int64_t K = h->K, M = h->M, N = 5 * K + M;
+    SolveWork s;
+    int rc = alloc_work(h, s, np, opt.restart);
+    if (rc) return rc;
+    // right-hand sides: b_I = A_T^T Phi_T with Phi = 1 on the plus nodes of port j
+    std::vector<cdbl> bh((size_t)np * N, 0.0);
+    std::vector<uint8_t> plus(M);
+    for (int j = 0; j < np; ++j) {
+        std::fill(plus.begin(), plus.end(), 0);
+        for (int32_t m : h->port_plus[j]) plus[m] = 1;
+        for (int64_t v = 0; v < K; ++v)
+            for (int a = 0; a < 5; ++a) {
+                double acc = 0;
+                for (int f = 0; f < 6; ++f)
+                    if (plus[h->node[v * 6 + f]]) acc += kFluxH[a][f];
+                bh[(size_t)j * N + a * K + v] = acc;
+            }
+    }
+    SVH_CUDA_TRY(h, cudaMemcpyAsync(s.B.p, bh.data(), bh.size() * 16, cudaMemcpyHostToDevice, h->stream));
+    int total_it = 0, total_ref = 0;
+    double worst = 0;
+    int status = SVH_OK;
+    std::vector<double> bnorm;
+    if ((rc = norms(h, s, static_cast<double2*>(s.B.p), bnorm))) return rc;
+    for (int f = 0; f < nfreq; ++f) {
+        const double omega = omegas[f];
+        const auto ts = std::chrono::steady_clock::now();
+        if ((rc = precond_setup(h, omega, opt.amg_tol))) return rc;
+        int nf = 0;
+        const int* fn = precond_free_nodes(h, &nf);
+        s.nf = nf;
+        std::vector<int32_t> fid(M, -1);
+        for (int i = 0; i < nf; ++i) fid[fn[i]] = i;
+        if ((rc = dev_upload(h, s.Yd, precond_Y(h), (size_t)5 * K * 8)) ||
+            (rc = dev_upload(h, s.freenodes, fn, (size_t)std::max(nf, 1) * 4)) ||
+            (rc = dev_upload(h, s.freeid, fid.data(), (size_t)M * 4)) ||
+            (rc = dev_alloc(h, s.E, (size_t)np * std::max(nf, 1) * 16)) ||
+            (rc = dev_alloc(h, s.Bs, (size_t)np * std::max(nf, 1) * 16)))
+            return rc;
+        setup_s += std::chrono::duration<double>(std::chrono::steady_clock::now() - ts).count();
+        double2* X = static_cast<double2*>(s.X.p);
+        double2* R = static_cast<double2*>(s.R.p);
+        double2* W = static_cast<double2*>(s.W.p);
+        const int64_t blk = (int64_t)np * N;
+        SVH_CUDA_TRY(h, cudaMemsetAsync(X, 0, blk * 16, h->stream));
+        std::vector<double> rn;
+        double rel = 1.0;
+        for (int ref = 0; ref <= opt.max_refinements; ++ref) {
+            // true residual with the FP64 product
+            if ((rc = apply_op(h, s, omega, X, W, SVH_FP64))) return rc;
+            SVH_CUDA_TRY(h, cudaMemcpyAsync(R, s.B.p, blk * 16, cudaMemcpyDeviceToDevice, h->stream));
+            k_sub<<<blocks_for(blk), 256, 0, h->stream>>>(R, W, blk);
+            if ((rc = norms(h, s, R, rn))) return rc;
+            rel = 0;
+            for (int r = 0; r < np; ++r) rel = std::max(rel, bnorm[r] > 0 ? rn[r] / bnorm[r] : 0.0);
+            if (rel <= opt.rre || ref == opt.max_refinements) break;
+            std::vector<double> tol(np);
+            for (int r = 0; r < np; ++r) {
+                const double need = rn[r] > 0 ? 0.5 * opt.rre * bnorm[r] / rn[r] : 1.0;
+                tol[r] = opt.inner_precision == SVH_FP64 ? need : std::max(need, 1e-5);
+            }
+            int its = 0;
+            if ((rc = fgmres(h, s, omega, opt.inner_precision, tol, opt.max_iterations, its))) return rc;
+            total_it += its;
+            ++total_ref;
+            k_add<<<blocks_for(blk), 256, 0, h->stream>>>(X, static_cast<double2*>(s.D.p), blk);
+        }
+        worst = std::max(worst, rel);
+        if (rel > opt.rre) status = SVH_ERR_NOT_CONVERGED;
+        // port admittance from the node rows of the unmasked product (A I)
+        if ((rc = apply_op(h, s, omega, X, W, SVH_FP64, 0))) return rc;
+        std::vector<cdbl> w(blk);
+        SVH_CUDA_TRY(h, cudaMemcpyAsync(w.data(), W, blk * 16, cudaMemcpyDeviceToHost, h->stream));
+        SVH_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+        std::vector<cdbl> Y((size_t)np * np);
+        for (int j = 0; j < np; ++j)
+            for (int p = 0; p < np; ++p) {
+                cdbl acc = 0;
+                for (int32_t m : h->port_plus[p]) acc += w[(size_t)j * N + 5 * K + m];
+                Y[(size_t)p * np + j] = acc;
+            }
+        // Z = Y^{-1} by Gauss-Jordan with partial pivoting
+        std::vector<cdbl> A(Y), Zi((size_t)np * np, 0.0);
+        for (int i = 0; i < np; ++i) Zi[(size_t)i * np + i] = 1.0;
+        for (int c = 0; c < np; ++c) {
+            int piv = c;
+            for (int r = c + 1; r < np; ++r)
+                if (std::abs(A[(size_t)r * np + c]) > std::abs(A[(size_t)piv * np + c])) piv = r;
+            if (std::abs(A[(size_t)piv * np + c]) == 0) return set_err(h, SVH_ERR_SINGULAR, "svh_solve: singular port admittance");
+            for (int k = 0; k < np; ++k) {
+                std::swap(A[(size_t)c * np + k], A[(size_t)piv * np + k]);
+                std::swap(Zi[(size_t)c * np + k], Zi[(size_t)piv * np + k]);
+            }
+            const cdbl d = A[(size_t)c * np + c];
+            for (int k = 0; k < np; ++k) { A[(size_t)c * np + k] /= d; Zi[(size_t)c * np + k] /= d; }
+            for (int r = 0; r < np; ++r) {
+                if (r == c) continue;
+                const cdbl fct = A[(size_t)r * np + c];
+                if (fct == cdbl(0)) continue;
+                for (int k = 0; k < np; ++k) {
+                    A[(size_t)r * np + k] -= fct * A[(size_t)c * np + k];
+                    Zi[(size_t)r * np + k] -= fct * Zi[(size_t)c * np + k];
+                }
+            }
+        }
+        for (int i = 0; i < np * np; ++i) {
+            Zport[((size_t)f * np * np + i) * 2] = Zi[i].real();
+            Zport[((size_t)f * np * np + i) * 2 + 1] = Zi[i].imag();
+        }
+        // keep the last solutions (host) for svh_get_solution
+        h->last_x.resize((size_t)blk * 2);
+        SVH_CUDA_TRY(h, cudaMemcpyAsync(h->last_x.data(), X, blk * 16, cudaMemcpyDeviceToHost, h->stream));
+        SVH_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+        h->last_nb = np;
+    }
+    if (st) {
+        st->iterations = total_it;
+        st->refinements = total_ref;
+        st->amg_levels = precond_levels(h);
+        st->amg_avg_iterations = precond_avg_iters(h);
+        st->final_rre = worst;
+        st->setup_seconds = setup_s;
+        st->solve_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() - setup_s;
+    }
+    if (status) set_err(h, status, "svh_solve: relative residual above rre after the refinement budget");
+    return status;
+}
+
+int svh_get_solution(const svh_handle* hh, int port, double* x) {
+    const Handle* h = reinterpret_cast<const Handle*>(hh);
+    if (!h || !x) return SVH_ERR_ARG;
+    if (h->last_nb == 0) return SVH_ERR_STATE;
+    if (port < 0 || port >= h->last_nb) return SVH_ERR_ARG;
+    const int64_t N = 5 * h->K + h->M;
+    std::memcpy(x, h->last_x.data() + (size_t)port * N * 2, (size_t)N * 16);
+    return SVH_OK;
+}
+
+int svh_precond_apply(svh_handle* hh, double omega, int nb, const double* in, double* out) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h || !in || !out || nb <= 0 || !(omega > 0)) return SVH_ERR_ARG;
+    int rc = precond_setup(h, omega, 1e-12);
+    if (rc) return rc;
+    return precond_apply_host(h, nb, in, out);
+}
+
+}  // extern "C"

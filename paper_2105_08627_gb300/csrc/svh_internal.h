@@ -77,6 +77,13 @@ struct Handle {
     int prof_max = 0, prof_calls = 0;
     std::vector<cudaEvent_t> prof_ev;   // [prof_max][SVH_NPASS + 1]
 
+    // ---- sparse preconditioner (amg.cpp), built per frequency by the solver
+    void* precond = nullptr;
+
+    // ---- last solve (svh_get_solution)
+    std::vector<double> last_x;   // [nb][N] complex interleaved
+    int last_nb = 0;
+
     // ---- scratch for the matvec
     DevBuf d_B1, d_B2;
     DevBuf d_xin, d_yout;              // staging for svh_matvec_host
@@ -98,6 +105,15 @@ int launch_matvec_on(Handle* h, double omega, int nb, const void* x, void* y, in
 void matvec_scratch_bytes(const Handle* h, int nb, int precision, size_t* b1, size_t* b2);
 // quadrature of the unit kernels (kernels_gen.cu): fills T[7][Kz][Ky][Kx] (host)
 int generate_toeplitz_device(Handle* h, std::vector<double>& T);
+// sparse preconditioner (amg.cpp)
+void precond_free(Handle* h);
+int precond_setup(Handle* h, double omega, double tol);
+int precond_schur_solve(Handle* h, int nb, const double* e, double* b);
+const double* precond_Y(Handle* h);
+const int* precond_free_nodes(Handle* h, int* nf);
+int precond_levels(Handle* h);
+double precond_avg_iters(Handle* h);
+int precond_apply_host(Handle* h, int nb, const double* in, double* out);
 // Tucker rebuild (tucker.cu)
 int launch_tucker_rebuild(Handle* h);
 

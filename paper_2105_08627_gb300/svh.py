@@ -42,6 +42,17 @@ class svh_port(C.Structure):
                 ("n_minus", C.c_int32), ("minus", C.POINTER(C.c_int32))]
 
 
+class svh_options(C.Structure):
+    _fields_ = [("restart", C.c_int32), ("max_iterations", C.c_int32), ("max_refinements", C.c_int32),
+                ("inner_precision", C.c_int32), ("rre", C.c_double), ("amg_tol", C.c_double)]
+
+
+class svh_stats(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("refinements", C.c_int32), ("amg_levels", C.c_int32),
+                ("amg_avg_iterations", C.c_double), ("final_rre", C.c_double), ("setup_seconds", C.c_double),
+                ("solve_seconds", C.c_double)]
+
+
 class svh_grid_info(C.Structure):
     _fields_ = [("Kx", C.c_int32), ("Ky", C.c_int32), ("Kz", C.c_int32),
                 ("Px", C.c_int32), ("Py", C.c_int32), ("Pz", C.c_int32),
@@ -80,11 +91,16 @@ SIGNATURES = {
     "svh_rebuild_spectra": (C.c_int, [_P]),
     "svh_matvec": (C.c_int, [_P, C.c_double, C.c_int, _P, _P, C.c_int]),
     "svh_matvec_host": (C.c_int, [_P, C.c_double, C.c_int, _P, _P, C.c_int]),
+    "svh_default_options": (None, [C.POINTER(svh_options)]),
+    "svh_solve": (C.c_int, [_P, _DP, C.c_int, C.POINTER(svh_options), _DP, C.POINTER(svh_stats)]),
+    "svh_get_solution": (C.c_int, [_P, C.c_int, _DP]),
+    "svh_precond_apply": (C.c_int, [_P, C.c_double, C.c_int, _DP, _DP]),
     "svh_matvec_noalloc": (C.c_int, [_P, C.c_double, C.c_int, _P, _P, C.c_int]),
     "svh_profile_begin": (C.c_int, [_P, C.c_int]),
     "svh_profile_end": (C.c_int, [_P, _DP, _I32P]),
     "svh_host_face_nodes": (C.c_int, [C.c_int, C.c_int, C.c_int, _U8P, _I64P, _I64P, _I32P]),
     "svh_host_spectra": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _DP, _DP]),
+    "svh_host_amg_solve": (C.c_int, [C.c_int, _I32P, _I32P, _DP, _DP, _DP, C.c_double, C.c_int, _I32P, _I32P]),
     "svh_host_tucker_svd": (C.c_int, [_DP, C.c_int, C.c_int, C.c_int, C.c_double, _I32P, _DP, _DP, _DP, _DP]),
 }
 
@@ -141,6 +157,21 @@ def host_spectra(T, P):
     S = np.empty((7, Pz // 2 + 1, Py // 2 + 1, Px // 2 + 1))
     _check_host(lib().svh_host_spectra(Kx, Ky, Kz, Px, Py, Pz, _dp(T), _dp(S)), "svh_host_spectra")
     return S
+
+
+def host_amg_solve(S, b, tol=1e-8, maxit=500):
+    """x = S^-1 b by the library's AMG-preconditioned CG (S: scipy CSR, SPD) -> (x, iters, levels)."""
+    S = S.tocsr()
+    rp = np.ascontiguousarray(S.indptr, np.int32)
+    ci = np.ascontiguousarray(S.indices, np.int32)
+    v = np.ascontiguousarray(S.data, np.float64)
+    b = np.ascontiguousarray(b, np.float64)
+    x = np.zeros_like(b)
+    it = C.c_int32()
+    lv = C.c_int32()
+    _check_host(lib().svh_host_amg_solve(S.shape[0], _i32p(rp), _i32p(ci), _dp(v), _dp(b), _dp(x), tol, maxit,
+                                         C.byref(it), C.byref(lv)), "svh_host_amg_solve")
+    return x, it.value, lv.value
 
 
 def host_tucker_svd(O, tol):
@@ -300,6 +331,44 @@ class Handle:
         """svh_matvec_noalloc: the product on the library's fixed 64 MiB device scratch (no allocation)."""
         self._ck(lib().svh_matvec_noalloc(self._h, float(omega), int(nb), _P(x_ptr), _P(y_ptr), int(precision)),
                  "svh_matvec_noalloc")
+
+    def solve(self, freqs, **opts):
+        """Port impedances at the given frequencies (Hz) -> dict(Z[f,p,q], L = Im Z / omega, R, stats).
+
+        opts override svh_options fields (restart, max_iterations, max_refinements,
+        inner_precision, rre, amg_tol). Raises SVHError on failure; a solve that
+        stops above rre raises with code SVH_ERR_NOT_CONVERGED unless
+        allow_unconverged=True."""
+        allow = opts.pop("allow_unconverged", False)
+        o = svh_options()
+        lib().svh_default_options(C.byref(o))
+        for k, v in opts.items():
+            setattr(o, k, v)
+        freqs = np.atleast_1d(np.asarray(freqs, np.float64))
+        om = np.ascontiguousarray(2 * np.pi * freqs)
+        npt = self.info()["nports"]
+        Z = np.zeros((freqs.size, npt, npt, 2))
+        st = svh_stats()
+        rc = lib().svh_solve(self._h, _dp(om), om.size, C.byref(o), _dp(Z), C.byref(st))
+        if rc != SVH_OK and not (allow and rc == SVH_ERR_NOT_CONVERGED):
+            self._ck(rc, "svh_solve")
+        Zc = Z[..., 0] + 1j * Z[..., 1]
+        stats = {f: getattr(st, f) for f, _ in svh_stats._fields_}
+        stats["status"] = rc
+        return {"Z": Zc, "L": Zc.imag / om[:, None, None], "R": Zc.real, "stats": stats}
+
+    def solution(self, port):
+        N = self.info()["N"]
+        x = np.empty(2 * N)
+        self._ck(lib().svh_get_solution(self._h, port, _dp(x)), "svh_get_solution")
+        return x[0::2] + 1j * x[1::2]
+
+    def precond_apply(self, omega, v):
+        v = np.ascontiguousarray(np.atleast_2d(v), np.complex128)
+        out = np.empty_like(v)
+        self._ck(lib().svh_precond_apply(self._h, float(omega), v.shape[0], v.ctypes.data_as(_DP),
+                                         out.ctypes.data_as(_DP)), "svh_precond_apply")
+        return out
 
     PASSES = ("tucker_rebuild", "x_fwd", "y_fwd", "z_pass", "y_inv", "x_inv_epilogue", "node_rows")
 

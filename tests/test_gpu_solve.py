@@ -1,0 +1,129 @@
+"""GPU port solves (Eq. 7 with the Eq. 12-15 preconditioner, GMRES of Sec. III)
+against the CPU oracle through the C ABI.
+
+Tolerances: port impedance / inductance 1e-6 relative (the bound stated for
+the inductance after refinement); solution vectors 1e-6 relative in the
+2-norm; the preconditioner apply 1e-9 (both sides solve S to 1e-12)."""
+import numpy as np
+import pytest
+
+import closed_forms as cf
+import svh_synth as S
+from gpu_util import handle_for
+from oracle import geometry as G
+from oracle import greens as gr
+from oracle import operator as op
+from oracle import solve as so
+from oracle import twofluid as tf
+
+pytestmark = pytest.mark.gpu
+L_TOL = 1e-6
+
+
+def _two_bars():
+    s = S.bar(12, 9, 3, 1, 10, 1, 2, 0, 1, name="two_bars")
+    s2 = S.bar(12, 9, 3, 1, 10, 5, 7, 0, 1)
+    s.occ |= s2.occ
+    s.lam += s2.lam
+    s.sigma0 += s2.sigma0
+    s.ports += s2.ports
+    return s
+
+
+def test_precond_apply_matches_oracle():
+    s = S.strip_cfg1()
+    h = handle_for(s)
+    g = G.build_grid(s)
+    T = gr.toeplitz_signed(s.Kx, s.Ky, s.Kz)
+    P = (32, 32, 8)
+    om = 2 * np.pi * 1e9
+    ps = so.PortSystem(g, op.spectra(T, P), P, om)
+    K = g.K
+    rng = np.random.default_rng(3)
+    v = S.random_complex(4, (2, g.N))
+    out = h.precond_apply(om, v)
+    for b in range(2):
+        ref = ps.precond(np.concatenate([v[b, :5 * K], v[b, 5 * K + ps.free]]))
+        got = np.concatenate([out[b, :5 * K], out[b, 5 * K + ps.free]])
+        assert np.linalg.norm(got - ref) <= 1e-9 * np.linalg.norm(ref)
+        fixed = np.flatnonzero(ps.term)
+        assert np.array_equal(out[b, 5 * K + fixed], v[b, 5 * K + fixed])
+    h.close()
+
+
+@pytest.mark.parametrize("inner", ["fp32", "fp64"])
+def test_strip_port_impedance_vs_oracle(inner):
+    from paper_2105_08627_gb300 import svh
+    s = S.strip_cfg1()
+    ref = so.port_inductance(s, rre=1e-10)
+    h = handle_for(s)
+    res = h.solve([1e9], inner_precision=svh.SVH_FP32 if inner == "fp32" else svh.SVH_FP64)
+    Z = res["Z"][0]
+    assert abs(Z[0, 0] - ref["Z"][0, 0]) <= L_TOL * abs(ref["Z"][0, 0])
+    assert abs(res["L"][0, 0, 0] - ref["L"][0, 0]) <= L_TOL * ref["L"][0, 0]
+    assert res["stats"]["final_rre"] <= 1e-8
+    x = h.solution(0)
+    xr = np.zeros(ref["grid"].N, complex)
+    ps = ref["system"]
+    xr[:5 * ps.g.K] = ref["x"][0][:5 * ps.g.K]
+    xr[5 * ps.g.K + ps.free] = ref["x"][0][5 * ps.g.K:]
+    assert np.linalg.norm(x - xr) <= 1e-6 * np.linalg.norm(xr)
+    h.close()
+
+
+def test_two_port_inductance_matrix_vs_oracle():
+    s = _two_bars()
+    h = handle_for(s)
+    res = h.solve([2e9, 5e9])
+    for fi, f in enumerate((2e9, 5e9)):
+        r = so.port_inductance(s, freq=f, rre=1e-10)
+        Z = res["Z"][fi]
+        assert np.abs(Z - r["Z"]).max() <= L_TOL * np.abs(r["Z"]).max()
+        assert abs(Z[0, 1] - Z[1, 0]) <= 1e-7 * abs(Z[0, 1])          # reciprocity
+    L = res["L"][0]
+    assert L[0, 0] > 0 and L[1, 1] > 0 and 0 < L[0, 1] < np.sqrt(L[0, 0] * L[1, 1])
+    h.close()
+
+
+def test_dc_bar_exact_partial_inductance():
+    """Normal bar at low skin parameter: L equals the closed-form partial self-inductance."""
+    a, b, c = 8, 3, 2
+    s = S.bar(a + 2, b + 2, c + 2, 1, a, 1, b, 1, c, dx=0.1e-6, lam=1e3, sigma0=3e6, freqs=(1e9,))
+    h = handle_for(s)
+    res = h.solve([1e9], rre=1e-12, inner_precision=1)
+    Lbar = tf.MU0 * s.dx * cf.bar_self(a, b, c) / (4 * np.pi * b * b * c * c)
+    assert abs(res["L"][0, 0, 0] - Lbar) <= 2e-5 * Lbar
+    h.close()
+
+
+def test_floating_island_gets_a_gauge():
+    s = S.bar(10, 8, 3, 0, 7, 0, 1, 0, 0)
+    s.occ[2, 5:7, 0:5] = 1
+    s.lam[2, 5:7, 0:5] = 90e-9
+    s.sigma0[2, 5:7, 0:5] = 1e7
+    ref = so.port_inductance(s, rre=1e-10)
+    h = handle_for(s)
+    assert h.info()["n_fixed_nodes"] == len(ref["grid"].port_plus[0]) + len(ref["grid"].port_minus[0]) + 1
+    res = h.solve([1e9])
+    assert abs(res["Z"][0, 0, 0] - ref["Z"][0, 0]) <= L_TOL * abs(ref["Z"][0, 0])
+    h.close()
+
+
+@pytest.mark.slow
+def test_meander_256x256x8_solve_true_residual():
+    """cfg 2 solve (FP32 inner, FP64 refinement); the oracle's FP64 product checks the residual."""
+    s = S.meander_cfg2()
+    h = handle_for(s)
+    res = h.solve([1e9])
+    assert res["stats"]["final_rre"] <= 1e-8
+    x = h.solution(0)
+    g = G.build_grid(s)
+    T = gr.toeplitz_octant(g.Kx, g.Ky, g.Kz)
+    P = (512, 512, 16)
+    ps = so.PortSystem(g, op.spectra(gr.signed_from_octant(T), P), P, 2 * np.pi * 1e9)
+    xr = np.concatenate([x[:5 * g.K], x[5 * g.K + ps.free]])
+    b = ps.rhs(0)
+    rel = np.linalg.norm(b - ps.matvec(xr)) / np.linalg.norm(b)
+    assert rel <= 2e-8, rel
+    assert res["L"][0, 0, 0] > 0
+    h.close()
