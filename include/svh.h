@@ -207,6 +207,18 @@ int svh_solve(svh_handle* h, const double* omegas, int nfreq, const svh_options*
 /* Solution vector x[N] (complex interleaved double) of port `port` at the
  * last frequency of the last svh_solve (fixed-node potentials are 0). */
 int svh_get_solution(const svh_handle* h, int port, double* x);
+/* Per-voxel materials (voxel order, length K): London depth (m, > 0) and
+ * normal conductivity (S/m, >= 0). Replaces those given to svh_setup_grid
+ * (kernels and FFT sizes are unaffected; the next svh_solve uses them). */
+int svh_set_materials(svh_handle* h, const double* lambda_vox, const double* sigma0_vox);
+int svh_get_materials(const svh_handle* h, double* lambda_vox, double* sigma0_vox);
+/* Adjoint gradient of L_ij = Im(Zport_ij)/omega at the last frequency of the
+ * last svh_solve with respect to each voxel's lambda (dL_dlambda[K], H/m) and
+ * sigma0 (dL_dsigma0[K], may be NULL). Uses the stored forward solutions as
+ * the adjoint ones (negating the continuity rows makes Eq. 7 complex
+ * symmetric): dZ_ij/dp_k = sum_beta dz^beta_k/dp_k w_i w_j, w_i = sum_p
+ * Z_ip I_p, with z^beta the two-fluid diagonal (Eq. 3, 9, 22-23). */
+int svh_grad_inductance(svh_handle* h, int i, int j, double* dL_dlambda, double* dL_dsigma0);
 /* Host reference of the preconditioner apply out = P in (Eq. 13-15) at
  * omega for nb vectors of length N (complex interleaved double), with the
  * Schur solves run to 1e-12 (for tests). */

@@ -597,6 +597,8 @@ int svh_solve(svh_handle* hh, const double* omegas, int nfreq, const svh_options
         SVH_CUDA_TRY(h, cudaMemcpyAsync(h->last_x.data(), X, blk * 16, cudaMemcpyDeviceToHost, h->stream));
         SVH_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
         h->last_nb = np;
+        h->last_omega = omega;
+        h->last_Z.assign(Zport + (size_t)f * np * np * 2, Zport + (size_t)(f + 1) * np * np * 2);
     }
     if (st) {
         st->iterations = total_it;

@@ -82,6 +82,8 @@ struct Handle {
 
     // ---- last solve (svh_get_solution)
     std::vector<double> last_x;   // [nb][N] complex interleaved
+    std::vector<double> last_Z;   // [nb][nb] complex interleaved, at last_omega
+    double last_omega = 0;
     int last_nb = 0;
 
     // ---- scratch for the matvec

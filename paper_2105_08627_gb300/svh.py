@@ -95,6 +95,9 @@ SIGNATURES = {
     "svh_solve": (C.c_int, [_P, _DP, C.c_int, C.POINTER(svh_options), _DP, C.POINTER(svh_stats)]),
     "svh_get_solution": (C.c_int, [_P, C.c_int, _DP]),
     "svh_precond_apply": (C.c_int, [_P, C.c_double, C.c_int, _DP, _DP]),
+    "svh_set_materials": (C.c_int, [_P, _DP, _DP]),
+    "svh_get_materials": (C.c_int, [_P, _DP, _DP]),
+    "svh_grad_inductance": (C.c_int, [_P, C.c_int, C.c_int, _DP, _DP]),
     "svh_matvec_noalloc": (C.c_int, [_P, C.c_double, C.c_int, _P, _P, C.c_int]),
     "svh_profile_begin": (C.c_int, [_P, C.c_int]),
     "svh_profile_end": (C.c_int, [_P, _DP, _I32P]),
@@ -356,6 +359,24 @@ class Handle:
         stats = {f: getattr(st, f) for f, _ in svh_stats._fields_}
         stats["status"] = rc
         return {"Z": Zc, "L": Zc.imag / om[:, None, None], "R": Zc.real, "stats": stats}
+
+    def set_materials(self, lam_vox, sigma0_vox):
+        lam = np.ascontiguousarray(lam_vox, np.float64)
+        sig = np.ascontiguousarray(sigma0_vox, np.float64)
+        self._ck(lib().svh_set_materials(self._h, _dp(lam), _dp(sig)), "svh_set_materials")
+
+    def materials(self):
+        K = self.info()["K"]
+        lam, sig = np.empty(K), np.empty(K)
+        self._ck(lib().svh_get_materials(self._h, _dp(lam), _dp(sig)), "svh_get_materials")
+        return lam, sig
+
+    def grad_inductance(self, i, j):
+        """(dL_ij/dlambda[K], dL_ij/dsigma0[K]) at the last solved frequency (adjoint)."""
+        K = self.info()["K"]
+        gl, gs = np.empty(K), np.empty(K)
+        self._ck(lib().svh_grad_inductance(self._h, i, j, _dp(gl), _dp(gs)), "svh_grad_inductance")
+        return gl, gs
 
     def solution(self, port):
         N = self.info()["N"]
