@@ -52,6 +52,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
+    p.add_argument("--no-solve", action="store_true", help="skip the whole-solve timing block")
+    p.add_argument("--with-batch", action="store_true",
+                   help="also time a graph-captured batched product over the 64 cfg-3 structures")
     return p.parse_args()
 
 
@@ -164,20 +167,29 @@ def pass_bytes(info, nb, csz):
     }
 
 
+def kernel_sources_sha():
+    """Hash of every library source: ncu counters recorded for another version are not used."""
+    import hashlib
+    d = os.path.join(ROOT, "paper_2105_08627_gb300", "csrc")
+    hsh = hashlib.sha256()
+    for f in sorted(os.listdir(d)):
+        hsh.update(open(os.path.join(d, f), "rb").read())
+    return hsh.hexdigest()[:16]
+
+
 def traffic_from_profiles(kernel, workload):
     """DRAM bytes per launch recorded from ncu for this kernel and workload, if current."""
     import hashlib
     path = os.path.join(ROOT, "profiles", f"traffic_{workload}.txt")
     if not os.path.exists(path):
         return None
-    src = open(os.path.join(ROOT, "paper_2105_08627_gb300", "csrc", "matvec.cu"), "rb").read()
-    sha = hashlib.sha256(src).hexdigest()[:16]
+    sha = kernel_sources_sha()
     vals = {}
     for line in open(path):
         if ":" in line and not line.startswith("#"):
             k, v = line.split(":", 1)
             vals[k.strip()] = v.strip()
-    if vals.get("matvec_cu_sha256_16") != sha:
+    if vals.get("csrc_sha256_16") != sha:
         return None
     v = vals.get(f"{kernel}_dram_bytes_per_launch")
     return float(v) if v else None
@@ -258,6 +270,56 @@ def time_steps(h, torch, omega, x, y, steps, flush, profile=False):
     torch.cuda.synchronize()
     prof = h.profile_end() if profile else None
     return sum(a.elapsed_time(b) for a, b in evs), prof
+
+
+def run_batch(torch, svh, S, args):
+    """Graph-captured batched FP32 product over the 64 seeded cfg-3 structures (ports batched per item)."""
+    items = S.batch_cfg3()
+    stream = torch.cuda.current_stream().cuda_stream
+    hs, xs, ys, oms = [], [], [], []
+    t0 = time.perf_counter()
+    for i, it in enumerate(items):
+        h = svh.Handle(0, stream)
+        h.setup_structure(it)
+        h.generate_toeplitz()
+        hs.append(h)
+    setup = time.perf_counter() - t0
+    b = svh.Batch(0)
+    nbs, kts = [], []
+    for i, (h, it) in enumerate(zip(hs, items)):
+        b.add(h)
+        info = h.info()
+        nb = max(1, info["nports"])
+        nbs.append(nb)
+        kts.append(info["Kx"] * info["Ky"] * info["Kz"])
+        xs.append(torch.from_numpy(S.random_complex(i, (nb, info["N"])).astype(np.complex64)).cuda())
+        ys.append(torch.empty_like(xs[-1]))
+        oms.append(2 * np.pi * it.freqs[i % 3])
+    # the batch API takes one nb for all items: use the smallest port count
+    nb = min(nbs)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(max(3, args.warmup)):
+        b.matvec(oms, xs, ys, svh.SVH_FP32, nb=nb)
+    b.sync()
+    bs = torch.cuda.ExternalStream(b.stream)
+    tot = 0.0
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(bs)
+        b.matvec(oms, xs, ys, svh.SVH_FP32, nb=nb)
+        e1.record(bs)
+        b.sync()
+        tot += e0.elapsed_time(e1)
+    vox = nb * sum(kts)
+    out = {"value": vox * args.steps / (tot / 1e3), "unit": UNIT, "ms_per_step": tot / args.steps,
+           "structures": len(items), "nb_per_structure": nb, "sum_Kt": int(sum(kts)),
+           "launch": "one CUDA graph per step (all structures)", "setup_s": setup}
+    b.close()
+    for h in hs:
+        h.close()
+    return out
 
 
 def run_svh(args):
@@ -341,6 +403,24 @@ def run_svh(args):
         e2e = {"value": ws * nb * Kt * args.steps / el, "unit": UNIT,
                "h2d_bytes_per_step": nb * N * 8, "d2h_bytes_per_step": nb * N * 8,
                "entry_point": "svh_matvec_host (pinned host buffers)"}
+    # whole port solve of the same structure (FP32 products inside FP64 refinement, RRE 1e-8)
+    solve = None
+    if not args.no_solve:
+        torch.cuda.synchronize()
+        h.set_kernel_mode(svh.SVH_KERNELS_RESIDENT)
+        t0 = time.perf_counter()
+        res = h.solve([s.freqs[0]])
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        st = res["stats"]
+        solve = {"seconds": wall, "setup_s": st["setup_seconds"], "iterations": st["iterations"],
+                 "refinements": st["refinements"], "final_rre": st["final_rre"],
+                 "amg_avg_cg_iterations": st["amg_avg_iterations"], "L_pH": float(res["L"][0, 0, 0] * 1e12),
+                 "note": "GMRES(50), FP32 products in FP64 refinement, host AMG-FCG Schur solves (1e-8)"}
+        h.set_kernel_mode(svh.SVH_KERNELS_TUCKER_REBUILD)
+    batch = None
+    if args.with_batch and rank == 0:
+        batch = run_batch(torch, svh, S, args)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(s)
@@ -355,7 +435,8 @@ def run_svh(args):
                           "tucker_tol": args.tucker_tol, "tucker_ranks_G00": ranks[0].tolist(),
                           "l2": "flushed before every step (512 MB write, outside the events)",
                           "parallelism": f"replicas x{ws}", "setup_s": t_setup},
-               "fp64": fp64, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+               "fp64": fp64, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "solve": solve,
+               "batch_cfg3": batch,
                "gpu_launches": launches_per_step * args.steps, "clocks": clocks}
         print(json.dumps(out), flush=True)
     h.close()

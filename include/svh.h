@@ -159,6 +159,13 @@ int svh_rebuild_spectra(svh_handle* h);
  * SVH_FP64. Asynchronous on the handle's stream. Requires kernels. */
 int svh_matvec(svh_handle* h, double omega, int nb, const void* x_dev, void* y_dev,
                int precision);
+/* Same product with a different angular frequency per batch item
+ * (omegas[nb], host memory): many ports and frequencies of one structure in
+ * one launch sequence. The kernel spectra do not depend on omega (the Green
+ * function is static, Sec. II.A); only the j omega mu dx scale and the
+ * two-fluid diagonal change per item. */
+int svh_matvec_omegas(svh_handle* h, const double* omegas, int nb, const void* x_dev, void* y_dev,
+                      int precision);
 /* Same product from and to host memory: copies x to the device, applies the
  * operator and copies y back before returning (synchronous). */
 int svh_matvec_host(svh_handle* h, double omega, int nb, const void* x, void* y,
@@ -223,6 +230,32 @@ int svh_grad_inductance(svh_handle* h, int i, int j, double* dL_dlambda, double*
  * omega for nb vectors of length N (complex interleaved double), with the
  * Schur solves run to 1e-12 (for tests). */
 int svh_precond_apply(svh_handle* h, double omega, int nb, const double* in, double* out);
+
+/* ---- Batches of independent structures (unevenly sized grids).
+ * A batch borrows handles (each set up with its grid, ports and kernels) and
+ * must be destroyed before them. svh_batch_matvec applies each structure's
+ * operator to its own nb vectors x_dev[i] -> y_dev[i] (device pointers, as
+ * svh_matvec) at angular frequency omegas[i]: the first call with a given
+ * set of arguments runs the products once and captures all of them into one
+ * CUDA graph on the batch stream; that call and later calls with the same
+ * arguments launch the graph (asynchronous; svh_batch_sync waits).
+ * svh_batch_solve runs svh_solve for every structure at the same
+ * frequencies with n_workers host threads (<= 0: 4), each on its own stream,
+ * so one structure's host preconditioner work overlaps the others' device
+ * work; Zports[i] receives structure i's nfreq*np_i*np_i complex values; the
+ * stats are summed (final_rre: the largest). */
+typedef struct svh_batch svh_batch;
+int svh_batch_create(svh_batch** b, int device);
+int svh_batch_destroy(svh_batch* b);
+const char* svh_batch_last_error(const svh_batch* b);
+int svh_batch_add(svh_batch* b, svh_handle* h);
+int svh_batch_size(const svh_batch* b);
+int svh_batch_matvec(svh_batch* b, const double* omegas, int nb, const void* const* x_dev, void* const* y_dev,
+                     int precision);
+int svh_batch_sync(svh_batch* b);
+void* svh_batch_stream(svh_batch* b);
+int svh_batch_solve(svh_batch* b, const double* omegas, int nfreq, const svh_options* opt, double* const* Zports,
+                    int n_workers, svh_stats* st);
 
 /* ---- Product for callers that cannot allocate device memory at call time.
  * (An interface of this library; the paper has no counterpart.)

@@ -43,8 +43,13 @@ struct AmgLevel {
     std::vector<int> agg;        // fine -> coarse index
     std::vector<int> crp, cidx;  // coarse index -> its fine indices (CSR), for a parallel restriction
     int nc = 0;
-    // workspaces (mutable: the cycle reuses them; one solve at a time per hierarchy)
-    mutable std::vector<double> r, rc, xc, v1, w1, rr, v2, w2;
+};
+
+// per-solve scratch of the cycle, one set per level (solves on one hierarchy
+// may run concurrently, each with its own workspace)
+struct AmgWork {
+    struct Lv { std::vector<double> r, rc, xc, v1, w1, rr, v2, w2; };
+    std::vector<Lv> lv;
 };
 
 struct Amg {
@@ -185,11 +190,6 @@ static bool amg_setup(const Csr& S, Amg& amg) {
         next.A = galerkin(L.A, L.agg, n2);
         amg.lv.push_back(std::move(next));
     }
-    for (auto& L : amg.lv) {
-        const int n = L.A.n;
-        L.r.assign(n, 0); L.rc.assign(L.nc, 0); L.xc.assign(L.nc, 0);
-        L.v1.assign(n, 0); L.w1.assign(n, 0); L.rr.assign(n, 0); L.v2.assign(n, 0); L.w2.assign(n, 0);
-    }
     // dense Cholesky of the coarsest operator
     const Csr& C = amg.lv.back().A;
     const int n = C.n;
@@ -246,24 +246,41 @@ static double dotp(const double* a, const double* b, int n) {
     return s;
 }
 
-static void kcycle(const Amg& amg, int l, const double* b, double* x);
+static void kcycle(const Amg& amg, AmgWork& wk, int l, const double* b, double* x);
+
+// size the workspace for this hierarchy (hierarchies of different frequencies
+// differ in their coarse levels, so every level's sizes are checked)
+static void work_init(const Amg& amg, AmgWork& wk) {
+    bool ok = wk.lv.size() == amg.lv.size();
+    for (size_t l = 0; ok && l < amg.lv.size(); ++l)
+        ok = wk.lv[l].r.size() == (size_t)amg.lv[l].A.n && wk.lv[l].rc.size() == (size_t)amg.lv[l].nc;
+    if (ok) return;
+    wk.lv.assign(amg.lv.size(), AmgWork::Lv());
+    for (size_t l = 0; l < amg.lv.size(); ++l) {
+        const int n = amg.lv[l].A.n, nc = amg.lv[l].nc;
+        auto& w = wk.lv[l];
+        w.r.assign(n, 0); w.rc.assign(nc, 0); w.xc.assign(nc, 0);
+        w.v1.assign(n, 0); w.w1.assign(n, 0); w.rr.assign(n, 0); w.v2.assign(n, 0); w.w2.assign(n, 0);
+    }
+}
 
 // Two steps of flexible CG on level l with the level-l cycle as
 // preconditioner: the K-cycle's Krylov acceleration of the coarse solve.
-static void coarse_krylov(const Amg& amg, int l, const double* b, double* x) {
+static void coarse_krylov(const Amg& amg, AmgWork& wk, int l, const double* b, double* x) {
     const AmgLevel& L = amg.lv[l];
     const Csr& A = L.A;
     const int n = A.n;
     if (l == (int)amg.lv.size() - 1) {
-        kcycle(amg, l, b, x);
+        kcycle(amg, wk, l, b, x);
         return;
     }
-    double* v1 = L.v1.data();
-    double* w1 = L.w1.data();
-    double* r = L.rr.data();
-    double* v2 = L.v2.data();
-    double* w2 = L.w2.data();
-    kcycle(amg, l, b, v1);
+    auto& W = wk.lv[l];
+    double* v1 = W.v1.data();
+    double* w1 = W.w1.data();
+    double* r = W.rr.data();
+    double* v2 = W.v2.data();
+    double* w2 = W.w2.data();
+    kcycle(amg, wk, l, b, v1);
     spmv(A, v1, w1);
     const double d11 = dotp(v1, w1, n);
     const double g1 = dotp(v1, b, n);
@@ -277,7 +294,7 @@ static void coarse_krylov(const Amg& amg, int l, const double* b, double* x) {
         for (int i = 0; i < n; ++i) x[i] = a1 * v1[i];
         return;
     }
-    kcycle(amg, l, r, v2);
+    kcycle(amg, wk, l, r, v2);
     spmv(A, v2, w2);
     // minimise the A-norm of the error over span{v1, v2} (2 x 2 Galerkin system)
     const double d12 = dotp(v1, w2, n), d22 = dotp(v2, w2, n);
@@ -294,16 +311,16 @@ static void coarse_krylov(const Amg& amg, int l, const double* b, double* x) {
 
 // K-cycle with zero initial guess: x ~= A_l^{-1} b. One l1-Jacobi sweep,
 // coarse correction by coarse_krylov on level l+1, one l1-Jacobi sweep.
-static void kcycle(const Amg& amg, int l, const double* b, double* x) {
+static void kcycle(const Amg& amg, AmgWork& wk, int l, const double* b, double* x) {
     const AmgLevel& L = amg.lv[l];
     const int n = L.A.n;
     if (l == (int)amg.lv.size() - 1) {
         coarse_solve(amg, b, x);
         return;
     }
-    double* r = L.r.data();
-    double* rc = L.rc.data();
-    double* xc = L.xc.data();
+    double* r = wk.lv[l].r.data();
+    double* rc = wk.lv[l].rc.data();
+    double* xc = wk.lv[l].xc.data();
 #pragma omp parallel for schedule(static) if (n > 20000)
     for (int i = 0; i < n; ++i) x[i] = b[i] / L.l1[i];
     spmv(L.A, x, r);
@@ -313,7 +330,7 @@ static void kcycle(const Amg& amg, int l, const double* b, double* x) {
         for (int p = L.crp[c]; p < L.crp[c + 1]; ++p) s += b[L.cidx[p]] - r[L.cidx[p]];
         rc[c] = s;
     }
-    coarse_krylov(amg, l + 1, rc, xc);
+    coarse_krylov(amg, wk, l + 1, rc, xc);
 #pragma omp parallel for schedule(static) if (n > 20000)
     for (int i = 0; i < n; ++i) x[i] += xc[L.agg[i]];
     spmv(L.A, x, r);
@@ -324,7 +341,8 @@ static void kcycle(const Amg& amg, int l, const double* b, double* x) {
 // Flexible CG (the K-cycle is not a fixed linear operator) for S x = b, x0 = 0;
 // each new direction is S-orthogonalised against the previous one.
 // Returns iterations, or -1 if not converged.
-static int pcg(const Csr& S, const Amg& amg, const double* b, double* x, double tol, int maxit) {
+static int pcg(const Csr& S, const Amg& amg, AmgWork& wk, const double* b, double* x, double tol, int maxit) {
+    work_init(amg, wk);
     const int n = S.n;
     std::vector<double> r(b, b + n), z(n), p(n), q(n), pold(n), qold(n);
     std::fill(x, x + n, 0.0);
@@ -332,7 +350,7 @@ static int pcg(const Csr& S, const Amg& amg, const double* b, double* x, double 
     if (nb == 0) return 0;
     double pq_old = 0;
     for (int it = 1; it <= maxit; ++it) {
-        kcycle(amg, 0, r.data(), z.data());
+        kcycle(amg, wk, 0, r.data(), z.data());
         p = z;
         if (it > 1) {
             const double beta = dotp(z.data(), qold.data(), n) / pq_old;
@@ -369,16 +387,22 @@ static const double kFlux[5][6] = {
     {-1, 1, 0, 0, 0, 0}, {0, 0, -1, 1, 0, 0}, {0, 0, 0, 0, -1, 1}, {0.5, 0.5, -0.5, -0.5, 0, 0}, {0.5, 0.5, 0.5, 0.5, -1, -1}};
 static const double kSbeta[5] = {1.0, 1.0, 1.0, 1.0 / 6.0, 0.5};
 
+// one Precond per frequency of the current solve (h->precond points to this)
+struct PrecondSet {
+    std::vector<Precond*> f;
+    ~PrecondSet() { for (Precond* p : f) delete p; }
+};
+
 void precond_free(Handle* h) {
-    delete static_cast<Precond*>(h->precond);
+    delete static_cast<PrecondSet*>(h->precond);
     h->precond = nullptr;
 }
 
+static Precond* P_at(Handle* h, int fi) { return static_cast<PrecondSet*>(h->precond)->f[fi]; }
+
 // Y = |diag Z| (Eq. 12) at omega: two-fluid diagonal plus the Green self term
 // j omega mu dx T_bb(0) (G00(0) for x, y, z; Qx+Qy for 2D; Qx+Qy+4Qz for 3D).
-int precond_setup(Handle* h, double omega, double tol) {
-    if (!h->have_grid || !h->have_kernels) return set_err(h, SVH_ERR_STATE, "preconditioner: grid and kernels needed");
-    precond_free(h);
+static int precond_setup_one(Handle* h, double omega, double tol, Precond*& out) {
     Precond* P = new Precond();
     P->omega = omega;
     P->tol = tol;
@@ -443,43 +467,83 @@ int precond_setup(Handle* h, double omega, double tol) {
         return set_err(h, SVH_ERR_SINGULAR, "preconditioner: coarsest Schur operator not positive definite "
                                             "(a conductor without terminal or gauge?)");
     }
-    h->precond = P;
+    out = P;
+    return SVH_OK;
+}
+
+int precond_setup(Handle* h, const double* omegas, int nfreq, double tol) {
+    if (!h->have_grid || !h->have_kernels) return set_err(h, SVH_ERR_STATE, "preconditioner: grid and kernels needed");
+    precond_free(h);
+    PrecondSet* set = new PrecondSet();
+    h->precond = set;
+    for (int f = 0; f < nfreq; ++f) {
+        Precond* P = nullptr;
+        int rc = precond_setup_one(h, omegas[f], tol, P);
+        if (rc) return rc;
+        set->f.push_back(P);
+    }
     return SVH_OK;
 }
 
 // b = S^{-1} e for nb complex right-hand sides given on the free nodes
-// (interleaved re, im; e[rhs][nf]); real and imaginary parts are two real solves.
-int precond_schur_solve(Handle* h, int nb, const double* e, double* b) {
-    Precond* P = static_cast<Precond*>(h->precond);
-    const int nf = P->S.n;
-    std::vector<double> re(nf), xr(nf);
-    for (int r = 0; r < nb; ++r)
-        for (int part = 0; part < 2; ++part) {
-            for (int i = 0; i < nf; ++i) re[i] = e[((size_t)r * nf + i) * 2 + part];
-            const int it = pcg(P->S, P->amg, re.data(), xr.data(), P->tol, P->maxit);
-            if (it < 0) return set_err(h, SVH_ERR_NOT_CONVERGED, "preconditioner: AMG-PCG did not converge");
-            P->pcg_calls++;
-            P->pcg_iters += it;
-            for (int i = 0; i < nf; ++i) b[((size_t)r * nf + i) * 2 + part] = xr[i];
+// (interleaved re, im; e[rhs][nf]); right-hand side r belongs to frequency
+// r / per_freq. Real and imaginary parts are two real solves.
+int precond_schur_solve(Handle* h, int nb, int per_freq, const double* e, double* b) {
+    const int nf = P_at(h, 0)->S.n;
+    const int ntask = 2 * nb;   // real and imaginary parts of every right-hand side
+    const int nthreads = omp_get_max_threads();
+    // many independent solves: one per thread (inner loops serial); few: inner loops parallel
+    const bool outer = ntask >= 4 && nthreads > 1;
+    std::vector<int> status(ntask, 0);
+    std::vector<long long> iters(ntask, 0);
+    auto one = [&](int t, AmgWork& wk, std::vector<double>& re, std::vector<double>& xr) {
+        const int r = t >> 1, part = t & 1;
+        Precond* P = P_at(h, r / per_freq);
+        for (int i = 0; i < nf; ++i) re[i] = e[((size_t)r * nf + i) * 2 + part];
+        const int it = pcg(P->S, P->amg, wk, re.data(), xr.data(), P->tol, P->maxit);
+        status[t] = it < 0;
+        iters[t] = it;
+        for (int i = 0; i < nf; ++i) b[((size_t)r * nf + i) * 2 + part] = xr[i];
+    };
+    if (outer) {
+#pragma omp parallel
+        {
+            AmgWork wk;
+            std::vector<double> re(nf), xr(nf);
+#pragma omp for schedule(dynamic, 1)
+            for (int t = 0; t < ntask; ++t) one(t, wk, re, xr);
         }
+    } else {
+        AmgWork wk;
+        std::vector<double> re(nf), xr(nf);
+        for (int t = 0; t < ntask; ++t) one(t, wk, re, xr);
+    }
+    for (int t = 0; t < ntask; ++t) {
+        if (status[t]) return set_err(h, SVH_ERR_NOT_CONVERGED, "preconditioner: AMG-PCG did not converge");
+        Precond* P = P_at(h, (t >> 1) / per_freq);
+        P->pcg_calls++;
+        P->pcg_iters += iters[t];
+    }
     return SVH_OK;
 }
 
-const double* precond_Y(Handle* h) { return static_cast<Precond*>(h->precond)->Yd.data(); }
+const double* precond_Y(Handle* h, int fi) { return P_at(h, fi)->Yd.data(); }
 const int* precond_free_nodes(Handle* h, int* nf) {
-    Precond* P = static_cast<Precond*>(h->precond);
+    Precond* P = P_at(h, 0);
     *nf = (int)P->free_nodes.size();
     return P->free_nodes.data();
 }
-int precond_levels(Handle* h) { return h->precond ? (int)static_cast<Precond*>(h->precond)->amg.lv.size() : 0; }
+int precond_levels(Handle* h) { return h->precond ? (int)P_at(h, 0)->amg.lv.size() : 0; }
 double precond_avg_iters(Handle* h) {
-    Precond* P = static_cast<Precond*>(h->precond);
-    return P && P->pcg_calls ? (double)P->pcg_iters / P->pcg_calls : 0.0;
+    if (!h->precond) return 0.0;
+    long long c = 0, it = 0;
+    for (Precond* P : static_cast<PrecondSet*>(h->precond)->f) { c += P->pcg_calls; it += P->pcg_iters; }
+    return c ? (double)it / c : 0.0;
 }
 
 // host reference of the whole preconditioner apply (Eq. 13-15) for nb vectors of length N
 int precond_apply_host(Handle* h, int nb, const double* in, double* out) {
-    Precond* P = static_cast<Precond*>(h->precond);
+    Precond* P = P_at(h, 0);
     const int64_t K = h->K, M = h->M, N = 5 * K + M;
     const int nf = P->S.n;
     std::vector<double> e((size_t)nb * nf * 2), bsol((size_t)nb * nf * 2);
@@ -503,7 +567,7 @@ int precond_apply_host(Handle* h, int nb, const double* in, double* out) {
                 }
             }
     }
-    int rc = precond_schur_solve(h, nb, e.data(), bsol.data());
+    int rc = precond_schur_solve(h, nb, nb, e.data(), bsol.data());
     if (rc) return rc;
     for (int r = 0; r < nb; ++r) {
         const double* c = in + (size_t)r * N * 2;
@@ -549,7 +613,8 @@ extern "C" int svh_host_amg_solve(int n, const int32_t* rowptr, const int32_t* c
     S.v.assign(vals, vals + rowptr[n]);
     Amg amg;
     if (!amg_setup(S, amg)) return SVH_ERR_SINGULAR;
-    const int it = pcg(S, amg, b, x, tol, maxit);
+    AmgWork wk;
+    const int it = pcg(S, amg, wk, b, x, tol, maxit);
     if (iters) *iters = it;
     if (levels) *levels = (int)amg.lv.size();
     return it < 0 ? SVH_ERR_NOT_CONVERGED : SVH_OK;

@@ -40,6 +40,8 @@ struct PassArgs {
     int64_t nlines;          // nb * 5 * nrows
     int nb, nza, nrows, Kx, Ky, Kz, Px, Py, Pz, Hx, Hy, Hz;
     double omega, mu, dx, conv_scale;
+    const double* omegas;    // per-item angular frequency (device, nb entries) or nullptr
+    double inv_P;            // 1 / (Px Py Pz)
     int masked;
 };
 
@@ -64,18 +66,20 @@ __device__ __forceinline__ typename CT<T>::type epilogue(const PassArgs& a, int6
                                                          typename CT<T>::type cv) {
     using C = typename CT<T>::type;
     const C* xb = static_cast<const C*>(a.x) + b * a.Nvec;
+    const double om = a.omegas ? a.omegas[b] : a.omega;
+    const T cs = a.omegas ? (T)(om * a.mu * a.dx * a.inv_P) : (T)a.conv_scale;
     C val;
-    val.x = -(T)a.conv_scale * cv.y;
-    val.y = (T)a.conv_scale * cv.x;
+    val.x = -cs * cv.y;
+    val.y = cs * cv.x;
     // two-fluid c = a + j omega mu b (Eq. 22-23), z^beta = c s_beta / dx
     const T lm = (T)a.lam[vi], s0 = (T)a.sig0[vi];
-    const T wml2 = (T)(a.omega * a.mu) * lm * lm;
+    const T wml2 = (T)(om * a.mu) * lm * lm;
     const T tt = s0 * wml2;
     const T den = (T)1 + tt * tt;
     const T sb = be < 3 ? (T)1 : (be == 3 ? (T)(1.0 / 6.0) : (T)0.5);
     const T sc = sb / (T)a.dx;
     const T zr = s0 * wml2 * wml2 / den * sc;
-    const T zi = (T)(a.omega * a.mu) * (lm * lm / den) * sc;
+    const T zi = (T)(om * a.mu) * (lm * lm / den) * sc;
     const C I = xb[be * a.K + vi];
     val.x += zr * I.x - zi * I.y;
     val.y += zr * I.y + zi * I.x;

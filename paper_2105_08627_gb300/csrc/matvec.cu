@@ -228,9 +228,9 @@ __global__ void __launch_bounds__(NTHR) k_xinv(
     typename CT<T>::type* __restrict__ y, int64_t Nvec, int64_t K,
     const int32_t* __restrict__ vidx, const int32_t* __restrict__ rows, int nrows, int nza,
     int Kx, int Ky, const int32_t* __restrict__ node, const uint8_t* __restrict__ freem,
-    const double* __restrict__ lam, const double* __restrict__ sig0, double omega, double mu,
-    double dx, T conv_scale, int masked, FftPlan px, const typename CT<T>::type* __restrict__ twg,
-    int lpb, int64_t nlines) {
+    const double* __restrict__ lam, const double* __restrict__ sig0, double omega_all, double mu,
+    double dx, T conv_scale_all, const double* __restrict__ omegas, double inv_P, int masked, FftPlan px,
+    const typename CT<T>::type* __restrict__ twg, int lpb, int64_t nlines) {
     using C = typename CT<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* tw = reinterpret_cast<C*>(smem_raw);
@@ -259,6 +259,8 @@ __global__ void __launch_bounds__(NTHR) k_xinv(
         int be = (int)(ba - 5 * b);
         const C* xb = x + b * Nvec;
         C cv = buf[l * ld + n];
+        const double omega = omegas ? omegas[b] : omega_all;
+        const T conv_scale = omegas ? (T)(omega * mu * dx * inv_P) : conv_scale_all;
         // j * conv_scale * conv
         C val;
         val.x = -conv_scale * cv.y;
@@ -345,8 +347,8 @@ void matvec_scratch_bytes(const Handle* h, int nb, int precision, size_t* b1, si
 
 // The launch sequence on caller-provided intermediate grids B1, B2.
 template <typename T>
-static int run_matvec(Handle* h, double omega, int nb, const void* xv, void* yv, int masked, void* B1v,
-                      void* B2v, bool allow_rebuild) {
+static int run_matvec(Handle* h, double omega, const double* d_omegas, int nb, const void* xv, void* yv, int masked,
+                      void* B1v, void* B2v, bool allow_rebuild) {
     using C = typename CT<T>::type;
     constexpr int MAXPTS = Cfg<T>::MAXPTS;
     const C* x = static_cast<const C*>(xv);
@@ -385,6 +387,8 @@ static int run_matvec(Handle* h, double omega, int nb, const void* xv, void* yv,
     pa.Px = Px; pa.Py = Py; pa.Pz = Pz; pa.Hx = h->Hx; pa.Hy = h->Hy; pa.Hz = h->Hz;
     pa.omega = omega; pa.mu = mu0; pa.dx = h->dx;
     pa.conv_scale = omega * mu0 * h->dx / ((double)Px * Py * Pz);
+    pa.omegas = d_omegas;
+    pa.inv_P = 1.0 / ((double)Px * Py * Pz);
     pa.masked = masked;
 
     prof_mark(h, -1);
@@ -445,7 +449,7 @@ static int run_matvec(Handle* h, double omega, int nb, const void* xv, void* yv,
             B1, x, y, Nvec, K, vidx, rows, nrows, nza, h->Kx, h->Ky,
             static_cast<const int32_t*>(h->d_node.p), static_cast<const uint8_t*>(h->d_free.p),
             static_cast<const double*>(h->d_lam.p), static_cast<const double*>(h->d_sig0.p), omega, mu,
-            h->dx, conv_scale, masked, px, twx, lpb, nlines);
+            h->dx, conv_scale, d_omegas, 1.0 / ((double)Px * Py * Pz), masked, px, twx, lpb, nlines);
     }
     prof_mark(h, 5);
     // node rows
@@ -463,23 +467,23 @@ static int run_matvec(Handle* h, double omega, int nb, const void* xv, void* yv,
 
 // The library-allocated path: grows the handle's intermediate grids when needed.
 template <typename T>
-static int launch_matvec(Handle* h, double omega, int nb, const void* xv, void* yv, int masked) {
+static int launch_matvec(Handle* h, double omega, int nb, const void* xv, void* yv, int masked, const double* d_omegas) {
     size_t b1, b2;
     matvec_scratch_bytes(h, nb, std::is_same<T, float>::value ? SVH_FP32 : SVH_FP64, &b1, &b2);
     if (h->d_B1.bytes < b1) { int rc = dev_alloc(h, h->d_B1, b1); if (rc) return rc; }
     if (h->d_B2.bytes < b2) { int rc = dev_alloc(h, h->d_B2, b2); if (rc) return rc; }
-    return run_matvec<T>(h, omega, nb, xv, yv, masked, h->d_B1.p, h->d_B2.p, true);
+    return run_matvec<T>(h, omega, d_omegas, nb, xv, yv, masked, h->d_B1.p, h->d_B2.p, true);
 }
 
-int launch_matvec32(Handle* h, double omega, int nb, const void* x, void* y, int masked) {
-    return launch_matvec<float>(h, omega, nb, x, y, masked);
+int launch_matvec32(Handle* h, double omega, int nb, const void* x, void* y, int masked, const double* d_omegas) {
+    return launch_matvec<float>(h, omega, nb, x, y, masked, d_omegas);
 }
-int launch_matvec64(Handle* h, double omega, int nb, const void* x, void* y, int masked) {
-    return launch_matvec<double>(h, omega, nb, x, y, masked);
+int launch_matvec64(Handle* h, double omega, int nb, const void* x, void* y, int masked, const double* d_omegas) {
+    return launch_matvec<double>(h, omega, nb, x, y, masked, d_omegas);
 }
 int launch_matvec_on(Handle* h, double omega, int nb, const void* x, void* y, int precision, void* B1, void* B2) {
-    return precision == SVH_FP32 ? run_matvec<float>(h, omega, nb, x, y, 0, B1, B2, false)
-                                 : run_matvec<double>(h, omega, nb, x, y, 0, B1, B2, false);
+    return precision == SVH_FP32 ? run_matvec<float>(h, omega, nullptr, nb, x, y, 0, B1, B2, false)
+                                 : run_matvec<double>(h, omega, nullptr, nb, x, y, 0, B1, B2, false);
 }
 
 }  // namespace svh

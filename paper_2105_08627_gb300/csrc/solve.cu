@@ -17,6 +17,9 @@
 // classical Gram-Schmidt applied twice (CGS2) in FP64: each pass is one
 // batched dot-product kernel over the basis and one linear-combination kernel.
 // Givens rotations and the small least-squares solves run on the host.
+// Batching: every (frequency, port) pair is an item; one FGMRES runs all items
+// in lock-step with batched operator products (per-item omega: the spectra do
+// not depend on it), batched Arnoldi kernels and one AMG hierarchy per frequency.
 // Refinement: r = b - Kt x in FP64, inner FGMRES on Kt (FP32 products) to a
 // relative reduction of 1e-5 (or to the target), x += correction, until
 // ||r|| / ||b|| <= rre measured with the FP64 product (Sec. III: RRE 1e-8).
@@ -162,12 +165,13 @@ __global__ void k_sub(double2* __restrict__ a, const double2* __restrict__ b, in
 
 // Preconditioner, first half (Eq. 14 right-hand side): e_m = d_m - sum over the
 // voxel faces at free node m of flux * c / Y, for every free node (compact).
-__global__ void k_prec_pre(const double2* __restrict__ v, int64_t Nvec, int64_t K, const double* __restrict__ Y,
-                           const int32_t* __restrict__ free_nodes, int nf, const int32_t* __restrict__ ninc,
-                           double2* __restrict__ e) {
+__global__ void k_prec_pre(const double2* __restrict__ v, int64_t Nvec, int64_t K, const double* __restrict__ Yall,
+                           int per_freq, const int32_t* __restrict__ free_nodes, int nf,
+                           const int32_t* __restrict__ ninc, double2* __restrict__ e) {
     const int r = blockIdx.y;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nf) return;
+    const double* Y = Yall + (int64_t)(r / per_freq) * 5 * K;
     const double2* vr = v + (int64_t)r * Nvec;
     const int m = free_nodes[i];
     double2 acc = vr[5 * K + m];
@@ -190,11 +194,12 @@ __global__ void k_prec_pre(const double2* __restrict__ v, int64_t Nvec, int64_t 
 // Preconditioner, second half (Eq. 15): a = Y^{-1}(c + A_F^T b); potentials:
 // b on free nodes, the input value on fixed nodes (identity rows of Kt).
 __global__ void k_prec_post_vox(const double2* __restrict__ v, double2* __restrict__ out, int64_t Nvec, int64_t K,
-                                const double* __restrict__ Y, const int32_t* __restrict__ node,
+                                const double* __restrict__ Yall, int per_freq, const int32_t* __restrict__ node,
                                 const int32_t* __restrict__ free_id, const double2* __restrict__ b, int nf) {
     const int r = blockIdx.y;
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= 5 * K) return;
+    const double* Y = Yall + (int64_t)(r / per_freq) * 5 * K;
     const int a = (int)(t / K);
     const int64_t vx = t - a * K;
     const double2* vr = v + (int64_t)r * Nvec;
@@ -229,11 +234,13 @@ __global__ void k_prec_post_node(const double2* __restrict__ v, double2* __restr
 // preconditioner and operator product consume directly.
 struct SolveWork {
     int nb = 0, m = 0;
+    int per_freq = 1;        // items of one frequency (= number of ports)
     int64_t N = 0;
     int nf = 0;
-    DevBuf X, B, R, W, D, V, Z, T32a, T32b, part, hbuf, E, Bs, Yd, freeid, freenodes, scl;
+    DevBuf X, B, R, W, D, V, Z, T32a, T32b, part, hbuf, E, Bs, Yd, freeid, freenodes, scl, om;
     ~SolveWork() {
-        for (DevBuf* b : {&X, &B, &R, &W, &D, &V, &Z, &T32a, &T32b, &part, &hbuf, &E, &Bs, &Yd, &freeid, &freenodes, &scl})
+        for (DevBuf* b : {&X, &B, &R, &W, &D, &V, &Z, &T32a, &T32b, &part, &hbuf, &E, &Bs, &Yd, &freeid, &freenodes,
+                          &scl, &om})
             dev_free(*b);
     }
 };
@@ -284,18 +291,18 @@ static int norms(Handle* h, SolveWork& s, const double2* w, std::vector<double>&
 static int apply_precond(Handle* h, SolveWork& s, const double2* in, double2* out) {
     const int64_t K = h->K, M = h->M, N = s.N;
     const int nf = s.nf;
-    k_prec_pre<<<dim3(blocks_for(nf), s.nb), 256, 0, h->stream>>>(in, N, K, static_cast<double*>(s.Yd.p),
+    k_prec_pre<<<dim3(blocks_for(nf), s.nb), 256, 0, h->stream>>>(in, N, K, static_cast<double*>(s.Yd.p), s.per_freq,
                                                                      static_cast<int32_t*>(s.freenodes.p), nf,
                                                                      static_cast<int32_t*>(h->d_ninc.p),
                                                                      static_cast<double2*>(s.E.p));
     std::vector<double> e((size_t)s.nb * nf * 2), b((size_t)s.nb * nf * 2);
     SVH_CUDA_TRY(h, cudaMemcpyAsync(e.data(), s.E.p, e.size() * 8, cudaMemcpyDeviceToHost, h->stream));
     SVH_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
-    int rc = precond_schur_solve(h, s.nb, e.data(), b.data());
+    int rc = precond_schur_solve(h, s.nb, s.per_freq, e.data(), b.data());
     if (rc) return rc;
     SVH_CUDA_TRY(h, cudaMemcpyAsync(s.Bs.p, b.data(), b.size() * 8, cudaMemcpyHostToDevice, h->stream));
     k_prec_post_vox<<<dim3(blocks_for(5 * K), s.nb), 256, 0, h->stream>>>(
-        in, out, N, K, static_cast<double*>(s.Yd.p), static_cast<int32_t*>(h->d_node.p),
+        in, out, N, K, static_cast<double*>(s.Yd.p), s.per_freq, static_cast<int32_t*>(h->d_node.p),
         static_cast<int32_t*>(s.freeid.p), static_cast<double2*>(s.Bs.p), nf);
     k_prec_post_node<<<dim3(blocks_for(M), s.nb), 256, 0, h->stream>>>(in, out, N, K, M,
                                                                         static_cast<int32_t*>(s.freeid.p),
@@ -307,11 +314,12 @@ static int apply_precond(Handle* h, SolveWork& s, const double2* in, double2* ou
 // y = Kt x (masked operator): FP64 product, or FP32 product with conversions
 static int apply_op(Handle* h, SolveWork& s, double omega, const double2* x, double2* y, int prec, int masked = 1) {
     const int64_t n = (int64_t)s.nb * s.N;
-    if (prec == SVH_FP64) return launch_matvec64(h, omega, s.nb, x, y, masked);
+    const double* dom = static_cast<const double*>(s.om.p);
+    if (prec == SVH_FP64) return launch_matvec64(h, omega, s.nb, x, y, masked, dom);
     float2* a = static_cast<float2*>(s.T32a.p);
     float2* b = static_cast<float2*>(s.T32b.p);
     k_to32<<<blocks_for(n), 256, 0, h->stream>>>(x, a, n);
-    int rc = launch_matvec32(h, omega, s.nb, a, b, masked);
+    int rc = launch_matvec32(h, omega, s.nb, a, b, masked, dom);
     if (rc) return rc;
     k_to64<<<blocks_for(n), 256, 0, h->stream>>>(b, y, n);
     return SVH_OK;
@@ -482,13 +490,15 @@ int svh_solve(svh_handle* hh, const double* omegas, int nfreq, const svh_options
     for (int f = 0; f < nfreq; ++f)
         if (!(omegas[f] > 0) || !std::isfinite(omegas[f])) return set_err(h, SVH_ERR_ARG, "svh_solve: omega must be > 0");
     const auto t0 = std::chrono::steady_clock::now();
-    double setup_s = 0;
     const int64_t K = h->K, M = h->M, N = 5 * K + M;
+    // every (frequency, port) pair is one item of the batch: item r = f * np + p
+    const int nb = np * nfreq;
     SolveWork s;
-    int rc = alloc_work(h, s, np, opt.restart);
+    s.per_freq = np;
+    int rc = alloc_work(h, s, nb, opt.restart);
     if (rc) return rc;
-    // right-hand sides: b_I = A_T^T Phi_T with Phi = 1 on the plus nodes of port j
-    std::vector<cdbl> bh((size_t)np * N, 0.0);
+    // right-hand sides: b_I = A_T^T Phi_T with Phi = 1 on the plus nodes of port p (same at every frequency)
+    std::vector<cdbl> bh((size_t)nb * N, 0.0);
     std::vector<uint8_t> plus(M);
     for (int j = 0; j < np; ++j) {
         std::fill(plus.begin(), plus.end(), 0);
@@ -498,70 +508,73 @@ int svh_solve(svh_handle* hh, const double* omegas, int nfreq, const svh_options
                 double acc = 0;
                 for (int f = 0; f < 6; ++f)
                     if (plus[h->node[v * 6 + f]]) acc += kFluxH[a][f];
-                bh[(size_t)j * N + a * K + v] = acc;
+                for (int f = 0; f < nfreq; ++f) bh[((size_t)f * np + j) * N + a * K + v] = acc;
             }
     }
     SVH_CUDA_TRY(h, cudaMemcpyAsync(s.B.p, bh.data(), bh.size() * 16, cudaMemcpyHostToDevice, h->stream));
+    std::vector<double> item_om(nb);
+    for (int r = 0; r < nb; ++r) item_om[r] = omegas[r / np];
+    if ((rc = dev_upload(h, s.om, item_om.data(), (size_t)nb * 8))) return rc;
+    // preconditioners: one Schur complement and AMG hierarchy per frequency (Y depends on omega)
+    const auto ts = std::chrono::steady_clock::now();
+    if ((rc = precond_setup(h, omegas, nfreq, opt.amg_tol))) return rc;
+    int nf = 0;
+    const int* fn = precond_free_nodes(h, &nf);
+    s.nf = nf;
+    std::vector<int32_t> fid(M, -1);
+    for (int i = 0; i < nf; ++i) fid[fn[i]] = i;
+    std::vector<double> Yall((size_t)nfreq * 5 * K);
+    for (int f = 0; f < nfreq; ++f) std::memcpy(Yall.data() + (size_t)f * 5 * K, precond_Y(h, f), (size_t)5 * K * 8);
+    if ((rc = dev_upload(h, s.Yd, Yall.data(), Yall.size() * 8)) ||
+        (rc = dev_upload(h, s.freenodes, fn, (size_t)std::max(nf, 1) * 4)) ||
+        (rc = dev_upload(h, s.freeid, fid.data(), (size_t)M * 4)) ||
+        (rc = dev_alloc(h, s.E, (size_t)nb * std::max(nf, 1) * 16)) ||
+        (rc = dev_alloc(h, s.Bs, (size_t)nb * std::max(nf, 1) * 16)))
+        return rc;
+    const double setup_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - ts).count();
     int total_it = 0, total_ref = 0;
-    double worst = 0;
     int status = SVH_OK;
     std::vector<double> bnorm;
     if ((rc = norms(h, s, static_cast<double2*>(s.B.p), bnorm))) return rc;
-    for (int f = 0; f < nfreq; ++f) {
-        const double omega = omegas[f];
-        const auto ts = std::chrono::steady_clock::now();
-        if ((rc = precond_setup(h, omega, opt.amg_tol))) return rc;
-        int nf = 0;
-        const int* fn = precond_free_nodes(h, &nf);
-        s.nf = nf;
-        std::vector<int32_t> fid(M, -1);
-        for (int i = 0; i < nf; ++i) fid[fn[i]] = i;
-        if ((rc = dev_upload(h, s.Yd, precond_Y(h), (size_t)5 * K * 8)) ||
-            (rc = dev_upload(h, s.freenodes, fn, (size_t)std::max(nf, 1) * 4)) ||
-            (rc = dev_upload(h, s.freeid, fid.data(), (size_t)M * 4)) ||
-            (rc = dev_alloc(h, s.E, (size_t)np * std::max(nf, 1) * 16)) ||
-            (rc = dev_alloc(h, s.Bs, (size_t)np * std::max(nf, 1) * 16)))
-            return rc;
-        setup_s += std::chrono::duration<double>(std::chrono::steady_clock::now() - ts).count();
-        double2* X = static_cast<double2*>(s.X.p);
-        double2* R = static_cast<double2*>(s.R.p);
-        double2* W = static_cast<double2*>(s.W.p);
-        const int64_t blk = (int64_t)np * N;
-        SVH_CUDA_TRY(h, cudaMemsetAsync(X, 0, blk * 16, h->stream));
-        std::vector<double> rn;
-        double rel = 1.0;
-        for (int ref = 0; ref <= opt.max_refinements; ++ref) {
-            // true residual with the FP64 product
-            if ((rc = apply_op(h, s, omega, X, W, SVH_FP64))) return rc;
-            SVH_CUDA_TRY(h, cudaMemcpyAsync(R, s.B.p, blk * 16, cudaMemcpyDeviceToDevice, h->stream));
-            k_sub<<<blocks_for(blk), 256, 0, h->stream>>>(R, W, blk);
-            if ((rc = norms(h, s, R, rn))) return rc;
-            rel = 0;
-            for (int r = 0; r < np; ++r) rel = std::max(rel, bnorm[r] > 0 ? rn[r] / bnorm[r] : 0.0);
-            if (rel <= opt.rre || ref == opt.max_refinements) break;
-            std::vector<double> tol(np);
-            for (int r = 0; r < np; ++r) {
-                const double need = rn[r] > 0 ? 0.5 * opt.rre * bnorm[r] / rn[r] : 1.0;
-                tol[r] = opt.inner_precision == SVH_FP64 ? need : std::max(need, 1e-5);
-            }
-            int its = 0;
-            if ((rc = fgmres(h, s, omega, opt.inner_precision, tol, opt.max_iterations, its))) return rc;
-            total_it += its;
-            ++total_ref;
-            k_add<<<blocks_for(blk), 256, 0, h->stream>>>(X, static_cast<double2*>(s.D.p), blk);
+    double2* X = static_cast<double2*>(s.X.p);
+    double2* R = static_cast<double2*>(s.R.p);
+    double2* W = static_cast<double2*>(s.W.p);
+    const int64_t blk = (int64_t)nb * N;
+    SVH_CUDA_TRY(h, cudaMemsetAsync(X, 0, blk * 16, h->stream));
+    std::vector<double> rn;
+    double rel = 1.0;
+    for (int ref = 0; ref <= opt.max_refinements; ++ref) {
+        // true residual with the FP64 product
+        if ((rc = apply_op(h, s, omegas[0], X, W, SVH_FP64))) return rc;
+        SVH_CUDA_TRY(h, cudaMemcpyAsync(R, s.B.p, blk * 16, cudaMemcpyDeviceToDevice, h->stream));
+        k_sub<<<blocks_for(blk), 256, 0, h->stream>>>(R, W, blk);
+        if ((rc = norms(h, s, R, rn))) return rc;
+        rel = 0;
+        for (int r = 0; r < nb; ++r) rel = std::max(rel, bnorm[r] > 0 ? rn[r] / bnorm[r] : 0.0);
+        if (rel <= opt.rre || ref == opt.max_refinements) break;
+        std::vector<double> tol(nb);
+        for (int r = 0; r < nb; ++r) {
+            const double need = rn[r] > 0 ? 0.5 * opt.rre * bnorm[r] / rn[r] : 1.0;
+            tol[r] = opt.inner_precision == SVH_FP64 ? need : std::max(need, 1e-5);
         }
-        worst = std::max(worst, rel);
-        if (rel > opt.rre) status = SVH_ERR_NOT_CONVERGED;
-        // port admittance from the node rows of the unmasked product (A I)
-        if ((rc = apply_op(h, s, omega, X, W, SVH_FP64, 0))) return rc;
-        std::vector<cdbl> w(blk);
-        SVH_CUDA_TRY(h, cudaMemcpyAsync(w.data(), W, blk * 16, cudaMemcpyDeviceToHost, h->stream));
-        SVH_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+        int its = 0;
+        if ((rc = fgmres(h, s, omegas[0], opt.inner_precision, tol, opt.max_iterations, its))) return rc;
+        total_it += its;
+        ++total_ref;
+        k_add<<<blocks_for(blk), 256, 0, h->stream>>>(X, static_cast<double2*>(s.D.p), blk);
+    }
+    if (rel > opt.rre) status = SVH_ERR_NOT_CONVERGED;
+    // port admittance from the node rows of the unmasked product (A I)
+    if ((rc = apply_op(h, s, omegas[0], X, W, SVH_FP64, 0))) return rc;
+    std::vector<cdbl> w(blk);
+    SVH_CUDA_TRY(h, cudaMemcpyAsync(w.data(), W, blk * 16, cudaMemcpyDeviceToHost, h->stream));
+    SVH_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    for (int f = 0; f < nfreq; ++f) {
         std::vector<cdbl> Y((size_t)np * np);
         for (int j = 0; j < np; ++j)
             for (int p = 0; p < np; ++p) {
                 cdbl acc = 0;
-                for (int32_t m : h->port_plus[p]) acc += w[(size_t)j * N + 5 * K + m];
+                for (int32_t m : h->port_plus[p]) acc += w[((size_t)f * np + j) * N + 5 * K + m];
                 Y[(size_t)p * np + j] = acc;
             }
         // Z = Y^{-1} by Gauss-Jordan with partial pivoting
@@ -592,20 +605,22 @@ int svh_solve(svh_handle* hh, const double* omegas, int nfreq, const svh_options
             Zport[((size_t)f * np * np + i) * 2] = Zi[i].real();
             Zport[((size_t)f * np * np + i) * 2 + 1] = Zi[i].imag();
         }
-        // keep the last solutions (host) for svh_get_solution
-        h->last_x.resize((size_t)blk * 2);
-        SVH_CUDA_TRY(h, cudaMemcpyAsync(h->last_x.data(), X, blk * 16, cudaMemcpyDeviceToHost, h->stream));
-        SVH_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
-        h->last_nb = np;
-        h->last_omega = omega;
-        h->last_Z.assign(Zport + (size_t)f * np * np * 2, Zport + (size_t)(f + 1) * np * np * 2);
     }
+    // keep the solutions of the last frequency (host) for svh_get_solution and the adjoint
+    const int flast = nfreq - 1;
+    h->last_x.resize((size_t)np * N * 2);
+    SVH_CUDA_TRY(h, cudaMemcpyAsync(h->last_x.data(), X + (int64_t)flast * np * N, (size_t)np * N * 16,
+                                    cudaMemcpyDeviceToHost, h->stream));
+    SVH_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    h->last_nb = np;
+    h->last_omega = omegas[flast];
+    h->last_Z.assign(Zport + (size_t)flast * np * np * 2, Zport + (size_t)(flast + 1) * np * np * 2);
     if (st) {
         st->iterations = total_it;
         st->refinements = total_ref;
         st->amg_levels = precond_levels(h);
         st->amg_avg_iterations = precond_avg_iters(h);
-        st->final_rre = worst;
+        st->final_rre = rel;
         st->setup_seconds = setup_s;
         st->solve_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() - setup_s;
     }
@@ -626,7 +641,7 @@ int svh_get_solution(const svh_handle* hh, int port, double* x) {
 int svh_precond_apply(svh_handle* hh, double omega, int nb, const double* in, double* out) {
     Handle* h = reinterpret_cast<Handle*>(hh);
     if (!h || !in || !out || nb <= 0 || !(omega > 0)) return SVH_ERR_ARG;
-    int rc = precond_setup(h, omega, 1e-12);
+    int rc = precond_setup(h, &omega, 1, 1e-12);
     if (rc) return rc;
     return precond_apply_host(h, nb, in, out);
 }

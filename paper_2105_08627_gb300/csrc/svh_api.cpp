@@ -116,7 +116,7 @@ static void free_all(Handle* h) {
     prof_release(h);
     precond_free(h);
     for (DevBuf* b : {&h->d_vidx, &h->d_rows, &h->d_rowmask, &h->d_zlist, &h->d_node, &h->d_ninc,
-                      &h->d_free, &h->d_lam, &h->d_sig0, &h->d_B1, &h->d_B2, &h->d_xin, &h->d_yout})
+                      &h->d_free, &h->d_lam, &h->d_sig0, &h->d_B1, &h->d_B2, &h->d_xin, &h->d_yout, &h->d_omegas})
         dev_free(*b);
 }
 
@@ -793,6 +793,26 @@ int svh_matvec(svh_handle* hh, double omega, int nb, const void* x, void* y, int
     const char* yc = static_cast<const char*>(y);
     if (xc < yc + bytes && yc < xc + bytes) return set_err(h, SVH_ERR_ARG, "svh_matvec: x and y overlap");
     return precision == SVH_FP32 ? launch_matvec32(h, omega, nb, x, y, 0) : launch_matvec64(h, omega, nb, x, y, 0);
+}
+
+int svh_matvec_omegas(svh_handle* hh, const double* omegas, int nb, const void* x, void* y, int precision) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    HCHECK(h);
+    if (!h->have_grid || !h->have_kernels)
+        return set_err(h, SVH_ERR_STATE, "svh_matvec_omegas: grid and kernels must be set up first");
+    if (!omegas || nb <= 0 || !x || !y || (precision != SVH_FP32 && precision != SVH_FP64))
+        return set_err(h, SVH_ERR_ARG, "svh_matvec_omegas: bad arguments");
+    for (int b = 0; b < nb; ++b)
+        if (!(omegas[b] > 0) || !std::isfinite(omegas[b])) return set_err(h, SVH_ERR_ARG, "svh_matvec_omegas: omega must be > 0");
+    const size_t bytes = (size_t)nb * (5 * h->K + h->M) * (precision == SVH_FP32 ? 8 : 16);
+    const char* xc = static_cast<const char*>(x);
+    const char* yc = static_cast<const char*>(y);
+    if (xc < yc + bytes && yc < xc + bytes) return set_err(h, SVH_ERR_ARG, "svh_matvec_omegas: x and y overlap");
+    if (h->d_omegas.bytes < (size_t)nb * 8) { int rc = dev_alloc(h, h->d_omegas, (size_t)nb * 8); if (rc) return rc; }
+    SVH_CUDA_TRY(h, cudaMemcpyAsync(h->d_omegas.p, omegas, (size_t)nb * 8, cudaMemcpyHostToDevice, h->stream));
+    const double* dom = static_cast<const double*>(h->d_omegas.p);
+    return precision == SVH_FP32 ? launch_matvec32(h, omegas[0], nb, x, y, 0, dom)
+                                 : launch_matvec64(h, omegas[0], nb, x, y, 0, dom);
 }
 
 int svh_matvec_host(svh_handle* hh, double omega, int nb, const void* x, void* y, int precision) {

@@ -89,6 +89,7 @@ struct Handle {
     // ---- scratch for the matvec
     DevBuf d_B1, d_B2;
     DevBuf d_xin, d_yout;              // staging for svh_matvec_host
+    DevBuf d_omegas;                   // per-item frequencies for svh_matvec_omegas
 };
 
 int set_err(Handle* h, int code, const std::string& msg);
@@ -100,8 +101,11 @@ void dev_free(DevBuf& b);
 int dev_upload(Handle* h, DevBuf& b, const void* src, size_t bytes);
 
 // launchers (matvec.cu)
-int launch_matvec32(Handle* h, double omega, int nb, const void* x, void* y, int masked);
-int launch_matvec64(Handle* h, double omega, int nb, const void* x, void* y, int masked);
+// d_omegas (device, nb entries): per-item angular frequency; nullptr -> omega for all items
+int launch_matvec32(Handle* h, double omega, int nb, const void* x, void* y, int masked,
+                    const double* d_omegas = nullptr);
+int launch_matvec64(Handle* h, double omega, int nb, const void* x, void* y, int masked,
+                    const double* d_omegas = nullptr);
 // same product on caller-provided intermediate grids (no allocation, no Tucker restore)
 int launch_matvec_on(Handle* h, double omega, int nb, const void* x, void* y, int precision, void* B1, void* B2);
 void matvec_scratch_bytes(const Handle* h, int nb, int precision, size_t* b1, size_t* b2);
@@ -109,9 +113,9 @@ void matvec_scratch_bytes(const Handle* h, int nb, int precision, size_t* b1, si
 int generate_toeplitz_device(Handle* h, std::vector<double>& T);
 // sparse preconditioner (amg.cpp)
 void precond_free(Handle* h);
-int precond_setup(Handle* h, double omega, double tol);
-int precond_schur_solve(Handle* h, int nb, const double* e, double* b);
-const double* precond_Y(Handle* h);
+int precond_setup(Handle* h, const double* omegas, int nfreq, double tol);
+int precond_schur_solve(Handle* h, int nb, int per_freq, const double* e, double* b);
+const double* precond_Y(Handle* h, int freq_index);
 const int* precond_free_nodes(Handle* h, int* nf);
 int precond_levels(Handle* h);
 double precond_avg_iters(Handle* h);

@@ -91,6 +91,7 @@ SIGNATURES = {
     "svh_rebuild_spectra": (C.c_int, [_P]),
     "svh_matvec": (C.c_int, [_P, C.c_double, C.c_int, _P, _P, C.c_int]),
     "svh_matvec_host": (C.c_int, [_P, C.c_double, C.c_int, _P, _P, C.c_int]),
+    "svh_matvec_omegas": (C.c_int, [_P, _DP, C.c_int, _P, _P, C.c_int]),
     "svh_default_options": (None, [C.POINTER(svh_options)]),
     "svh_solve": (C.c_int, [_P, _DP, C.c_int, C.POINTER(svh_options), _DP, C.POINTER(svh_stats)]),
     "svh_get_solution": (C.c_int, [_P, C.c_int, _DP]),
@@ -99,6 +100,16 @@ SIGNATURES = {
     "svh_get_materials": (C.c_int, [_P, _DP, _DP]),
     "svh_grad_inductance": (C.c_int, [_P, C.c_int, C.c_int, _DP, _DP]),
     "svh_matvec_noalloc": (C.c_int, [_P, C.c_double, C.c_int, _P, _P, C.c_int]),
+    "svh_batch_create": (C.c_int, [C.POINTER(_P), C.c_int]),
+    "svh_batch_destroy": (C.c_int, [_P]),
+    "svh_batch_last_error": (C.c_char_p, [_P]),
+    "svh_batch_add": (C.c_int, [_P, _P]),
+    "svh_batch_size": (C.c_int, [_P]),
+    "svh_batch_matvec": (C.c_int, [_P, _DP, C.c_int, C.POINTER(_P), C.POINTER(_P), C.c_int]),
+    "svh_batch_sync": (C.c_int, [_P]),
+    "svh_batch_stream": (_P, [_P]),
+    "svh_batch_solve": (C.c_int, [_P, _DP, C.c_int, C.POINTER(svh_options), C.POINTER(_DP), C.c_int,
+                                  C.POINTER(svh_stats)]),
     "svh_profile_begin": (C.c_int, [_P, C.c_int]),
     "svh_profile_end": (C.c_int, [_P, _DP, _I32P]),
     "svh_host_face_nodes": (C.c_int, [C.c_int, C.c_int, C.c_int, _U8P, _I64P, _I64P, _I32P]),
@@ -403,6 +414,17 @@ class Handle:
         self._ck(lib().svh_profile_end(self._h, _dp(ms), C.byref(n)), "svh_profile_end")
         return dict(zip(self.PASSES, ms.tolist())), n.value
 
+    def matvec_omegas(self, omegas, x, y=None):
+        """Batched product with one angular frequency per item (x: (nb, N) CUDA tensor)."""
+        import torch
+        prec = {torch.complex64: SVH_FP32, torch.complex128: SVH_FP64}[x.dtype]
+        om = np.ascontiguousarray(omegas, np.float64)
+        if y is None:
+            y = torch.empty_like(x)
+        self._ck(lib().svh_matvec_omegas(self._h, _dp(om), om.size, _P(x.data_ptr()), _P(y.data_ptr()), prec),
+                 "svh_matvec_omegas")
+        return y
+
     def matvec_host(self, omega, x):
         """Host-memory product (copies in, applies, copies out); x complex64 or complex128 NumPy."""
         x = np.ascontiguousarray(x)
@@ -415,3 +437,63 @@ class Handle:
         self._ck(lib().svh_matvec_host(self._h, float(omega), nb, x.ctypes.data_as(_P), y.ctypes.data_as(_P), prec),
                  "svh_matvec_host")
         return y
+
+
+class Batch:
+    """Several structures (handles) applied or solved together (see svh_batch_* in include/svh.h)."""
+
+    def __init__(self, device=0):
+        self._b = _P()
+        rc = lib().svh_batch_create(C.byref(self._b), int(device))
+        if rc != SVH_OK:
+            raise SVHError(rc, "svh_batch_create failed")
+        self.handles = []
+
+    def _ck(self, rc, what):
+        if rc != SVH_OK:
+            msg = lib().svh_batch_last_error(self._b)
+            raise SVHError(rc, f"{what}: {msg.decode() if msg else ''}")
+
+    def add(self, handle):
+        self._ck(lib().svh_batch_add(self._b, handle._h), "svh_batch_add")
+        self.handles.append(handle)
+
+    def matvec(self, omegas, xs, ys, precision=SVH_FP32, nb=1):
+        om = np.ascontiguousarray(omegas, np.float64)
+        xp = (_P * len(xs))(*[x.data_ptr() for x in xs])
+        yp = (_P * len(ys))(*[y.data_ptr() for y in ys])
+        self._ck(lib().svh_batch_matvec(self._b, _dp(om), nb, xp, yp, precision), "svh_batch_matvec")
+
+    def sync(self):
+        self._ck(lib().svh_batch_sync(self._b), "svh_batch_sync")
+
+    @property
+    def stream(self):
+        return lib().svh_batch_stream(self._b)
+
+    def solve(self, freqs, n_workers=4, **opts):
+        o = svh_options()
+        lib().svh_default_options(C.byref(o))
+        for k, v in opts.items():
+            setattr(o, k, v)
+        freqs = np.atleast_1d(np.asarray(freqs, np.float64))
+        om = np.ascontiguousarray(2 * np.pi * freqs)
+        outs = [np.zeros((freqs.size, h.info()["nports"], h.info()["nports"], 2)) for h in self.handles]
+        ptrs = (_DP * len(outs))(*[_dp(z) for z in outs])
+        st = svh_stats()
+        self._ck(lib().svh_batch_solve(self._b, _dp(om), om.size, C.byref(o), ptrs, int(n_workers), C.byref(st)),
+                 "svh_batch_solve")
+        Zs = [z[..., 0] + 1j * z[..., 1] for z in outs]
+        return {"Z": Zs, "L": [z.imag / om[:, None, None] for z in Zs],
+                "stats": {f: getattr(st, f) for f, _ in svh_stats._fields_}}
+
+    def close(self):
+        if self._b:
+            lib().svh_batch_destroy(self._b)
+            self._b = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -26,7 +26,7 @@ def svh():
 def declared_functions():
     src = open(os.path.join(ROOT, "include", "svh.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"^\s*(?:int|void|const char\*)\s+(svh_\w+)\s*\(", src, flags=re.M)))
+    return sorted(set(re.findall(r"^\s*(?:int|void|const char)\s*\*?\s*(svh_\w+)\s*\(", src, flags=re.M)))
 
 
 def test_library_exports_every_declared_symbol(svh):
