@@ -197,6 +197,11 @@ def signed_from_octant(T):
     return out
 
 
+def kernels_at_offsets(D, n_duffy=16):
+    """The 7 unit kernels at arbitrary integer offsets D[n, 3] (x, y, z) -> [7, n]."""
+    return _toeplitz_from_offsets(np.asarray(D, float), n_duffy)
+
+
 def _toeplitz_from_offsets(D, n_duffy):
     """Kernels at many integer offsets D[n, 3] -> [7, n]."""
     out = np.zeros((7, D.shape[0]))

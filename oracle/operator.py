@@ -148,3 +148,36 @@ def apply_K_fft(grid, S7, xvec, omega, P, mu=twofluid.MU0, workers=-1):
     top = apply_Z_fft(grid, S7, I, omega, P, mu, workers).ravel() - grid.A.T @ Phi
     bot = grid.A @ I
     return np.concatenate([top, bot])
+
+
+def direct_rows(grid, x, omega, vox_rows, node_rows, mu=twofluid.MU0):
+    """Selected rows of the Eq. 7 product by direct summation (no FFT), for any x.
+
+    vox_rows: voxel indices l (all five basis rows of each are returned,
+    shape [5, len]); node_rows: node indices m (rows of A I). The sum runs
+    only over the non-zero entries of x, so sparse inputs are cheap at any
+    grid size."""
+    K, M = grid.K, grid.M
+    x = np.asarray(x, complex)
+    I = x[:5 * K].reshape(5, K)
+    Phi = x[5 * K:]
+    supp = np.flatnonzero(np.any(I != 0, axis=0))
+    vox_rows = np.asarray(vox_rows)
+    d = grid.pos[vox_rows][:, None, :] - grid.pos[supp][None, :, :]          # obs - src
+    T = greens.kernels_at_offsets(d.reshape(-1, 3)).reshape(7, vox_rows.size, supp.size)
+    out = np.zeros((5, vox_rows.size), complex)
+    scale = 1j * omega * mu * grid.dx
+    for b in range(5):
+        for a in range(5):
+            coef = BLOCKS[b, a]
+            if not coef.any():
+                continue
+            blk = np.tensordot(coef, T, axes=(0, 0))                      # [rows, supp]
+            out[b] += scale * (blk @ I[a, supp])
+    zd = twofluid.zdiag(omega, grid.lam[vox_rows], grid.sigma0[vox_rows], grid.dx, mu)
+    out += zd * I[:, vox_rows]
+    AT = grid.A.T.tocsr()
+    for b in range(5):
+        out[b] -= AT[b * K + vox_rows] @ Phi
+    nodes = grid.A.tocsr()[np.asarray(node_rows)] @ x[:5 * K]
+    return out, nodes

@@ -222,3 +222,32 @@ def test_meander_256x256x8_full_size():
     y32 = h.matvec(om, torch.from_numpy(x.astype(np.complex64)).cuda()).cpu().numpy().astype(np.complex128)
     _check_fp32(y32, yref)
     h.close()
+
+
+@pytest.mark.slow
+def test_esfq_512x512x24_sampled_rows():
+    """cfg 5 size (512x512x24, P = 1024x1024x48) in one FP64 and one FP32 product of a
+    sparse input (1500 voxels, 500 nodes); 60 voxel rows (all 5 bases) and 40 node
+    rows are summed directly by the oracle (no FFT)."""
+    torch = _torch()
+    from oracle import geometry as G
+    from oracle import operator as opo
+    s = S.esfq_cfg5()
+    g = G.build_grid(s)
+    h = handle_for(s)
+    rng = np.random.default_rng(505)
+    x = np.zeros(g.N, complex)
+    sup = rng.choice(g.K, 1500, replace=False)
+    for a in range(5):
+        x[a * g.K + sup] = S.random_complex(10 + a, 1500)
+    x[5 * g.K + rng.choice(g.M, 500, replace=False)] = S.random_complex(20, 500)
+    om = 2 * np.pi * 1e9
+    rows = np.concatenate([rng.choice(sup, 30, replace=False), rng.choice(g.K, 30, replace=False)])
+    nodes = rng.choice(g.M, 40, replace=False)
+    yv, yn = opo.direct_rows(g, x, om, rows, nodes)
+    ref = np.concatenate([yv.ravel(), yn])
+    for dt, tol in ((torch.complex128, 1e-10), (torch.complex64, 2e-5)):
+        y = h.matvec(om, torch.from_numpy(x).to(dt).cuda()).cpu().numpy().astype(np.complex128)
+        got = np.concatenate([np.stack([y[b * g.K + rows] for b in range(5)]).ravel(), y[5 * g.K + nodes]])
+        assert np.abs(got - ref).max() <= tol * np.abs(ref).max(), (dt, np.abs(got - ref).max() / np.abs(ref).max())
+    h.close()

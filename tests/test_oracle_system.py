@@ -302,3 +302,22 @@ def test_two_port_admittance_symmetric():
     assert abs(Y[0, 1] - Y[1, 0]) <= 1e-7 * abs(Y[0, 1])
     L = res["L"]
     assert L[0, 0] > 0 and L[1, 1] > 0 and 0 < L[0, 1] < np.sqrt(L[0, 0] * L[1, 1])
+
+
+def test_direct_rows_equal_dense_product(strip):
+    """The direct-summation rows used at full size agree with the dense product."""
+    s, g, T = strip
+    om = 2 * np.pi * 1e9
+    rng = np.random.default_rng(12)
+    x = np.zeros(g.N, complex)
+    sup = rng.choice(g.K, 30, replace=False)
+    for a in range(5):
+        x[a * g.K + sup] = S.random_complex(a, 30)
+    x[5 * g.K + rng.choice(g.M, 40, replace=False)] = S.random_complex(9, 40)
+    y = op.dense_K(g, T, om) @ x
+    rows = rng.choice(g.K, 25, replace=False)
+    nodes = rng.choice(g.M, 25, replace=False)
+    yv, yn = op.direct_rows(g, x, om, rows, nodes)
+    for b in range(5):
+        assert np.allclose(yv[b], y[b * g.K + rows], rtol=1e-12, atol=1e-12 * np.abs(y).max())
+    assert np.allclose(yn, y[5 * g.K + nodes], rtol=1e-12, atol=1e-12 * np.abs(y).max())
