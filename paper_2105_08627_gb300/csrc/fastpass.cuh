@@ -191,6 +191,131 @@ __global__ void __launch_bounds__(NT) k_xrow(const __grid_constant__ PassArgs a)
     }
 }
 
+// x inverse + epilogue, grouped: a block takes G (item, row) groups and the 5
+// basis lines of each, runs the inverse x FFT of all 5G lines, parks the kept
+// x < Kx values in shared memory and then finishes every voxel of its rows in
+// one thread for all five bases (voxel index, face nodes, lambda, sigma0 and
+// the two-fluid c are loaded or computed once per voxel, not once per basis).
+template <typename T, int N1, int N2, int NT>
+__global__ void __launch_bounds__(NT) k_xinv_grouped(const __grid_constant__ PassArgs a) {
+    using C = typename CT<T>::type;
+    constexpr int N = N1 * N2;
+    constexpr int L = NT / N2;              // lines per block (a multiple of 5)
+    constexpr int G = L / 5;                // (item, row) groups per block
+    constexpr int LDS = N1 + 1;
+    constexpr int TPT = (L * N1 + NT - 1) / NT;
+    static_assert(L % 5 == 0, "lines per block must hold whole groups of 5 bases");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* tw = reinterpret_cast<C*>(smem_raw);
+    C* buf = tw + N;
+    const C* twg = static_cast<const C*>(a.twx);
+    for (int i = threadIdx.x; i < N; i += NT) tw[i] = twg[i];
+    const int64_t ngroups = (int64_t)a.nb * a.nrows;
+    const int64_t g0 = (int64_t)blockIdx.x * G;
+    const int Kx = a.Kx;
+    {
+        const int l = threadIdx.x / N2, n2 = threadIdx.x % N2;
+        const int64_t g = g0 + l / 5;
+        const int be = l % 5;
+        C v[N1];
+        if (g < ngroups) {
+            const int64_t b = g / a.nrows;
+            const int row = a.rows[g - b * a.nrows];
+            const C* src = static_cast<const C*>(a.B1) + ((b * 5 + be) * a.nza * a.Ky + row) * (int64_t)N;
+#pragma unroll
+            for (int n1 = 0; n1 < N1; ++n1) v[n1] = src[n1 * N2 + n2];
+        } else {
+#pragma unroll
+            for (int n1 = 0; n1 < N1; ++n1) { v[n1].x = 0; v[n1].y = 0; }
+        }
+        reg_fft<N1, true>(v);
+        __syncthreads();
+#pragma unroll
+        for (int k1 = 1; k1 < N1; ++k1) {
+            const int m = (n2 * k1) % N;
+            if (m) v[k1] = cmulc(v[k1], tw[m]);
+        }
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) buf[(l * N2 + n2) * LDS + k1] = v[k1];
+    }
+    __syncthreads();
+    C u[TPT][N2];
+#pragma unroll
+    for (int it = 0; it < TPT; ++it) {
+        const int task = threadIdx.x + it * NT;
+        if (task < L * N1) {
+            const int l = task / N1, k1 = task % N1;
+#pragma unroll
+            for (int n2 = 0; n2 < N2; ++n2) u[it][n2] = buf[(l * N2 + n2) * LDS + k1];
+            reg_fft<N2, true>(u[it]);
+        }
+    }
+    __syncthreads();   // every step-3 read of buf is done; reuse it for the kept x < Kx values
+    const int LDX = Kx + 1;
+#pragma unroll
+    for (int it = 0; it < TPT; ++it) {
+        const int task = threadIdx.x + it * NT;
+        if (task < L * N1) {
+            const int l = task / N1, k1 = task % N1;
+#pragma unroll
+            for (int k2 = 0; k2 < N2; ++k2) {
+                const int k = k1 + N1 * k2;
+                if (k < Kx) buf[l * LDX + k] = u[it][k2];
+            }
+        }
+    }
+    __syncthreads();
+    const T inv_dx = (T)(1.0 / a.dx);
+    for (int task = threadIdx.x; task < G * Kx; task += NT) {
+        const int gl = task / Kx, x = task % Kx;
+        const int64_t g = g0 + gl;
+        if (g >= ngroups) continue;
+        const int64_t b = g / a.nrows;
+        const int row = a.rows[g - b * a.nrows];
+        const int vi = __ldg(a.vidx + (int64_t)row * Kx + x);
+        if (vi < 0) continue;
+        const double om = a.omegas ? a.omegas[b] : a.omega;
+        const T cs = a.omegas ? (T)(om * a.mu * a.dx * a.inv_P) : (T)a.conv_scale;
+        // two-fluid c = a + j omega mu b (Eq. 22-23), once per voxel
+        const T lm = (T)a.lam[vi], s0 = (T)a.sig0[vi];
+        const T wm = (T)(om * a.mu);
+        const T wml2 = wm * lm * lm;
+        const T tt = s0 * wml2;
+        const T den = (T)1 + tt * tt;
+        const T cre = s0 * wml2 * wml2 / den * inv_dx, cim = wm * (lm * lm / den) * inv_dx;
+        const C* xb = static_cast<const C*>(a.x) + b * a.Nvec;
+        C* yb = static_cast<C*>(a.y) + b * a.Nvec;
+        C ph[6];
+        const int32_t* nd = a.node + (int64_t)vi * 6;
+#pragma unroll
+        for (int f = 0; f < 6; ++f) {
+            const int m = nd[f];
+            if (!a.masked || a.freem[m]) ph[f] = xb[5 * a.K + m];
+            else { ph[f].x = 0; ph[f].y = 0; }
+        }
+#pragma unroll
+        for (int be = 0; be < 5; ++be) {
+            const C cv = buf[(gl * 5 + be) * LDX + x];
+            C val;
+            val.x = -cs * cv.y;
+            val.y = cs * cv.x;
+            const T sb = be < 3 ? (T)1 : (be == 3 ? (T)(1.0 / 6.0) : (T)0.5);
+            const C I = xb[be * a.K + vi];
+            val.x += sb * (cre * I.x - cim * I.y);
+            val.y += sb * (cre * I.y + cim * I.x);
+#pragma unroll
+            for (int f = 0; f < 6; ++f) {
+                const float fl = face_flux(be, f);
+                if (fl != 0.f) {
+                    val.x -= (T)fl * ph[f].x;
+                    val.y -= (T)fl * ph[f].y;
+                }
+            }
+            yb[be * a.K + vi] = val;
+        }
+    }
+}
+
 // ---------------------------------------------------------------- y passes (strided lines, kx tiles)
 // INV = false: B1 rows y < Ky (active) -> forward FFT -> B2 rows ky < Py.
 // INV = true : B2 -> inverse FFT -> B1 active rows y < Ky.
@@ -326,20 +451,34 @@ __global__ void __launch_bounds__(160) k_zpass_fast(const __grid_constant__ Pass
     }
     C* B2 = static_cast<C*>(a.B2);
     const int64_t plane = (int64_t)Py * Px;
+    // planes holding voxels: at most (Pz + 1) / 2 of them (Pz >= 2 Kz - 1)
+    constexpr int NZ = PZ / 2 + 1;
+    const int nza = a.nza;
+    int zl[NZ];
+#pragma unroll
+    for (int zi = 0; zi < NZ; ++zi) zl[zi] = zi < nza ? a.zlist[zi] : 0;
+    // the next item's active planes are fetched into registers while the
+    // current item is transformed, so their latency overlaps the FFTs
+    C pre[NZ];
+    auto fetch = [&](int b) {
+        const int64_t base = ((int64_t)(b * 5 + al) * nza * Py + ky) * Px + kx;
+#pragma unroll
+        for (int zi = 0; zi < NZ; ++zi)
+            if (ok && zi < nza) pre[zi] = B2[base + zi * plane];
+    };
+    fetch(0);
     C v[PZ];
     for (int b = 0; b < a.nb; ++b) {
-        __syncthreads();   // previous item done with buf (and spectra ready)
+        // own column only until the first barrier: the previous item's
+        // cross-column multiply finished before its second barrier
 #pragma unroll
-        for (int z = 0; z < PZ; ++z) { v[z].x = 0; v[z].y = 0; }
-        const int64_t base = ((int64_t)(b * 5 + al) * a.nza * Py + ky) * Px + kx;
-        if (ok) {
-            // planes holding voxels go to their z slot; the rest stays zero
+        for (int z = 0; z < PZ; ++z) { buf[al][z][lane].x = 0; buf[al][z][lane].y = 0; }
 #pragma unroll
-            for (int z = 0; z < PZ; ++z) buf[al][z][lane] = v[z];
-            for (int zi = 0; zi < a.nza; ++zi) buf[al][a.zlist[zi]][lane] = B2[base + zi * plane];
+        for (int zi = 0; zi < NZ; ++zi)
+            if (zi < nza && ok) buf[al][zl[zi]][lane] = pre[zi];
+        if (b + 1 < a.nb) fetch(b + 1);
 #pragma unroll
-            for (int z = 0; z < PZ; ++z) v[z] = buf[al][z][lane];
-        }
+        for (int z = 0; z < PZ; ++z) v[z] = buf[al][z][lane];
         reg_fft<PZ, false>(v);
 #pragma unroll
         for (int z = 0; z < PZ; ++z) buf[al][z][lane] = v[z];
@@ -361,7 +500,10 @@ __global__ void __launch_bounds__(160) k_zpass_fast(const __grid_constant__ Pass
         if (ok) {
 #pragma unroll
             for (int z = 0; z < PZ; ++z) buf[al][z][lane] = v[z];   // own column only
-            for (int zi = 0; zi < a.nza; ++zi) B2[base + zi * plane] = buf[al][a.zlist[zi]][lane];
+            const int64_t base = ((int64_t)(b * 5 + al) * nza * Py + ky) * Px + kx;
+#pragma unroll
+            for (int zi = 0; zi < NZ; ++zi)
+                if (zi < nza) B2[base + zi * plane] = buf[al][zl[zi]][lane];
         }
     }
 }
