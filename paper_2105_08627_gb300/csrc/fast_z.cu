@@ -9,6 +9,11 @@ static void run_z(const PassArgs& a, cudaStream_t s) {
     const size_t sm = (size_t)5 * PZ * 32 * sizeof(C) + (size_t)7 * PZ * 32 * sizeof(T);
     cudaFuncSetAttribute(k_zpass_fast<T, PZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     dim3 grid((a.Px + 31) / 32, a.Py);
+    if (a.zcontig && 2 * a.nza <= PZ) {
+        cudaFuncSetAttribute(k_zpass_half<T, PZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        k_zpass_half<T, PZ><<<grid, 160, sm, s>>>(a);
+        return;
+    }
     k_zpass_fast<T, PZ><<<grid, 160, sm, s>>>(a);
 }
 

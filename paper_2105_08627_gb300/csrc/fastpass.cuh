@@ -43,6 +43,7 @@ struct PassArgs {
     const double* omegas;    // per-item angular frequency (device, nb entries) or nullptr
     double inv_P;            // 1 / (Px Py Pz)
     int masked;
+    int zcontig;             // 1 when the active planes are consecutive
 };
 
 // outward flux of basis alpha through face f (-x,+x,-y,+y,-z,+z)
@@ -119,34 +120,41 @@ __global__ void __launch_bounds__(NT) k_xrow(const __grid_constant__ PassArgs a)
         const int l = threadIdx.x / N2, n2 = threadIdx.x % N2;
         const int64_t line = line0 + l;
         C v[N1];
-        if (line < a.nlines) {
-            const int64_t ba = line / a.nrows;
-            const int row = a.rows[line - ba * a.nrows];
-            if (!INV) {
+        if constexpr (!INV) {
+            // x < Kx <= N / 2: inputs n1 >= N1 / 2 are zero (input-pruned first stage)
+            C hv[N1 / 2];
+#pragma unroll
+            for (int n1 = 0; n1 < N1 / 2; ++n1) { hv[n1].x = 0; hv[n1].y = 0; }
+            if (line < a.nlines) {
+                const int64_t ba = line / a.nrows;
+                const int row = a.rows[line - ba * a.nrows];
                 const int64_t b = ba / 5;
                 const int al = (int)(ba - 5 * b);
                 const C* xb = static_cast<const C*>(a.x) + b * a.Nvec + al * a.K;
                 const int32_t* vr = a.vidx + (int64_t)row * a.Kx;
 #pragma unroll
-                for (int n1 = 0; n1 < N1; ++n1) {
+                for (int n1 = 0; n1 < N1 / 2; ++n1) {
                     const int n = n1 * N2 + n2;
-                    C z; z.x = 0; z.y = 0;
                     if (n < a.Kx) {
                         const int vi = __ldg(vr + n);
-                        if (vi >= 0) z = xb[vi];
+                        if (vi >= 0) hv[n1] = xb[vi];
                     }
-                    v[n1] = z;
                 }
-            } else {
+            }
+            reg_fft_lowin<N1, false>(hv, v);
+        } else {
+            if (line < a.nlines) {
+                const int64_t ba = line / a.nrows;
+                const int row = a.rows[line - ba * a.nrows];
                 const C* src = static_cast<const C*>(a.B1) + (ba * a.nza * a.Ky + row) * (int64_t)N;
 #pragma unroll
                 for (int n1 = 0; n1 < N1; ++n1) v[n1] = src[n1 * N2 + n2];
-            }
-        } else {
+            } else {
 #pragma unroll
-            for (int n1 = 0; n1 < N1; ++n1) { v[n1].x = 0; v[n1].y = 0; }
+                for (int n1 = 0; n1 < N1; ++n1) { v[n1].x = 0; v[n1].y = 0; }
+            }
+            reg_fft<N1, true>(v);
         }
-        reg_fft<N1, INV>(v);
         __syncthreads();   // twiddle table ready
 #pragma unroll
         for (int k1 = 1; k1 < N1; ++k1) {
@@ -167,24 +175,27 @@ __global__ void __launch_bounds__(NT) k_xrow(const __grid_constant__ PassArgs a)
         C u[N2];
 #pragma unroll
         for (int n2 = 0; n2 < N2; ++n2) u[n2] = buf[(l * N2 + n2) * LDS + k1];
-        reg_fft<N2, INV>(u);
         const int64_t ba = line / a.nrows;
         const int row = a.rows[line - ba * a.nrows];
-        if (!INV) {
+        if constexpr (!INV) {
+            reg_fft<N2, false>(u);
             C* dst = static_cast<C*>(a.B1) + (ba * a.nza * a.Ky + row) * (int64_t)N;
 #pragma unroll
             for (int k2 = 0; k2 < N2; ++k2) dst[k1 + N1 * k2] = u[k2];
         } else {
+            // only x = k1 + N1 k2 < Kx <= N / 2 is kept: k2 < N2 / 2 (output-pruned)
+            C w[N2 / 2];
+            reg_fft_lowout<N2, true>(u, w);
             const int64_t b = ba / 5;
             const int be = (int)(ba - 5 * b);
             const int32_t* vr = a.vidx + (int64_t)row * a.Kx;
             C* yb = static_cast<C*>(a.y) + b * a.Nvec + be * a.K;
 #pragma unroll
-            for (int k2 = 0; k2 < N2; ++k2) {
+            for (int k2 = 0; k2 < N2 / 2; ++k2) {
                 const int k = k1 + N1 * k2;
                 if (k < a.Kx) {
                     const int vi = __ldg(vr + k);
-                    if (vi >= 0) yb[vi] = epilogue<T>(a, b, be, vi, u[k2]);
+                    if (vi >= 0) yb[vi] = epilogue<T>(a, b, be, vi, w[k2]);
                 }
             }
         }
@@ -239,15 +250,17 @@ __global__ void __launch_bounds__(NT) k_xinv_grouped(const __grid_constant__ Pas
         for (int k1 = 0; k1 < N1; ++k1) buf[(l * N2 + n2) * LDS + k1] = v[k1];
     }
     __syncthreads();
-    C u[TPT][N2];
+    // only x = k1 + N1 k2 < Kx <= N / 2 is kept: k2 < N2 / 2 (output-pruned)
+    C u[TPT][N2 / 2];
 #pragma unroll
     for (int it = 0; it < TPT; ++it) {
         const int task = threadIdx.x + it * NT;
         if (task < L * N1) {
             const int l = task / N1, k1 = task % N1;
+            C t[N2];
 #pragma unroll
-            for (int n2 = 0; n2 < N2; ++n2) u[it][n2] = buf[(l * N2 + n2) * LDS + k1];
-            reg_fft<N2, true>(u[it]);
+            for (int n2 = 0; n2 < N2; ++n2) t[n2] = buf[(l * N2 + n2) * LDS + k1];
+            reg_fft_lowout<N2, true>(t, u[it]);
         }
     }
     __syncthreads();   // every step-3 read of buf is done; reuse it for the kept x < Kx values
@@ -258,7 +271,7 @@ __global__ void __launch_bounds__(NT) k_xinv_grouped(const __grid_constant__ Pas
         if (task < L * N1) {
             const int l = task / N1, k1 = task % N1;
 #pragma unroll
-            for (int k2 = 0; k2 < N2; ++k2) {
+            for (int k2 = 0; k2 < N2 / 2; ++k2) {
                 const int k = k1 + N1 * k2;
                 if (k < Kx) buf[l * LDX + k] = u[it][k2];
             }
@@ -339,15 +352,18 @@ __global__ void __launch_bounds__(NT) k_ycol_fast(const __grid_constant__ PassAr
         const int c = threadIdx.x % TB, n2 = threadIdx.x / TB;
         const bool colok = kx0 + c < Px;
         C v[N1];
-        if (!INV) {
+        if constexpr (!INV) {
+            // y < Ky <= N / 2: inputs n1 >= N1 / 2 are zero (input-pruned first stage)
             const C* src = static_cast<const C*>(a.B1) + ((ba * a.nza + zi) * (int64_t)a.Ky) * Px + kx0 + c;
+            C hv[N1 / 2];
 #pragma unroll
-            for (int n1 = 0; n1 < N1; ++n1) {
+            for (int n1 = 0; n1 < N1 / 2; ++n1) {
                 const int n = n1 * N2 + n2;
                 C z; z.x = 0; z.y = 0;
                 if (colok && n < a.Ky && rm[n]) z = src[(int64_t)n * Px];
-                v[n1] = z;
+                hv[n1] = z;
             }
+            reg_fft_lowin<N1, false>(hv, v);
         } else {
             const C* src = static_cast<const C*>(a.B2) + ((ba * a.nza + zi) * (int64_t)N) * Px + kx0 + c;
 #pragma unroll
@@ -356,8 +372,8 @@ __global__ void __launch_bounds__(NT) k_ycol_fast(const __grid_constant__ PassAr
                 if (colok) z = src[(int64_t)(n1 * N2 + n2) * Px];
                 v[n1] = z;
             }
+            reg_fft<N1, true>(v);
         }
-        reg_fft<N1, INV>(v);
         __syncthreads();
 #pragma unroll
         for (int k1 = 1; k1 < N1; ++k1) {
@@ -377,17 +393,20 @@ __global__ void __launch_bounds__(NT) k_ycol_fast(const __grid_constant__ PassAr
         C u[N2];
 #pragma unroll
         for (int n2 = 0; n2 < N2; ++n2) u[n2] = buf[(n2 * N1 + k1) * TB + c];
-        reg_fft<N2, INV>(u);
-        if (!INV) {
+        if constexpr (!INV) {
+            reg_fft<N2, false>(u);
             C* dst = static_cast<C*>(a.B2) + ((ba * a.nza + zi) * (int64_t)N) * Px + kx0 + c;
 #pragma unroll
             for (int k2 = 0; k2 < N2; ++k2) dst[(int64_t)(k1 + N1 * k2) * Px] = u[k2];
         } else {
+            // only y = k1 + N1 k2 < Ky <= N / 2 is kept: k2 < N2 / 2 (output-pruned)
+            C w[N2 / 2];
+            reg_fft_lowout<N2, true>(u, w);
             C* dst = static_cast<C*>(a.B1) + ((ba * a.nza + zi) * (int64_t)a.Ky) * Px + kx0 + c;
 #pragma unroll
-            for (int k2 = 0; k2 < N2; ++k2) {
+            for (int k2 = 0; k2 < N2 / 2; ++k2) {
                 const int k = k1 + N1 * k2;
-                if (k < a.Ky && rm[k]) dst[(int64_t)k * Px] = u[k2];
+                if (k < a.Ky && rm[k]) dst[(int64_t)k * Px] = w[k2];
             }
         }
     }
@@ -504,6 +523,96 @@ __global__ void __launch_bounds__(160) k_zpass_fast(const __grid_constant__ Pass
 #pragma unroll
             for (int zi = 0; zi < NZ; ++zi)
                 if (zi < nza) B2[base + zi * plane] = buf[al][zl[zi]][lane];
+        }
+    }
+}
+
+// Contiguous active planes z0 .. z0 + nza - 1 (the usual case: layers and the
+// vias between them). A cyclic convolution commutes with shifts, so each
+// pencil is shifted by -z0: its inputs then sit at [0, nza), inside the lower
+// half of the PZ points (nza <= Kz <= PZ / 2), and only outputs [0, nza) are
+// kept. The forward transform is then input-pruned and the inverse
+// output-pruned (reg_fft_lowin / reg_fft_lowout), the pencil never passes
+// through shared memory except for the cross-basis multiply, and the spectra
+// indices kz are unchanged (a shift only multiplies each spectrum by a phase
+// that the inverse removes).
+template <typename T, int PZ>
+__global__ void __launch_bounds__(160) k_zpass_half(const __grid_constant__ PassArgs a) {
+    using C = typename CT<T>::type;
+    constexpr int H = PZ / 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C(*buf)[PZ][32] = reinterpret_cast<C(*)[PZ][32]>(smem_raw);            // [5][PZ][32]
+    T(*sp)[PZ][32] = reinterpret_cast<T(*)[PZ][32]>(smem_raw + sizeof(C) * 5 * PZ * 32);  // [7][PZ][32]
+    const int al = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int kx0 = blockIdx.x * 32;
+    const int ky = blockIdx.y;
+    const int kx = kx0 + lane;
+    const bool ok = kx < a.Px;
+    const int Px = a.Px, Py = a.Py;
+    {
+        const T* spec = static_cast<const T*>(a.spec);
+        const int64_t Sk = (int64_t)a.Hx * a.Hy * a.Hz;
+        const int ay = min(ky, Py - ky);
+        const T sgy = (2 * ky <= Py) ? (T)1 : (T)-1;
+        for (int task = threadIdx.x; task < PZ * 32; task += 160) {
+            const int kz = task >> 5, ln = task & 31;
+            const int kxx = min(kx0 + ln, Px - 1);
+            const int ax = min(kxx, Px - kxx), az = min(kz, PZ - kz);
+            const T sgx = (2 * kxx <= Px) ? (T)1 : (T)-1;
+            const T sgz = (2 * kz <= PZ) ? (T)1 : (T)-1;
+            const int64_t off = ((int64_t)az * a.Hy + ay) * a.Hx + ax;
+            sp[0][kz][ln] = __ldg(spec + off);
+            sp[1][kz][ln] = sgx * __ldg(spec + Sk + off);
+            sp[2][kz][ln] = sgy * __ldg(spec + 2 * Sk + off);
+            sp[3][kz][ln] = sgz * __ldg(spec + 3 * Sk + off);
+            sp[4][kz][ln] = __ldg(spec + 4 * Sk + off);
+            sp[5][kz][ln] = __ldg(spec + 5 * Sk + off);
+            sp[6][kz][ln] = __ldg(spec + 6 * Sk + off);
+        }
+    }
+    C* B2 = static_cast<C*>(a.B2);
+    const int64_t plane = (int64_t)Py * Px;
+    const int nza = a.nza;
+    C pre[H];
+    auto fetch = [&](int b) {
+        const int64_t base = ((int64_t)(b * 5 + al) * nza * Py + ky) * Px + kx;
+#pragma unroll
+        for (int zi = 0; zi < H; ++zi) {
+            C z; z.x = 0; z.y = 0;
+            if (ok && zi < nza) z = B2[base + zi * plane];
+            pre[zi] = z;
+        }
+    };
+    fetch(0);
+    for (int b = 0; b < a.nb; ++b) {
+        {
+            C v[PZ];
+            reg_fft_lowin<PZ, false>(pre, v);
+            if (b + 1 < a.nb) fetch(b + 1);
+#pragma unroll
+            for (int z = 0; z < PZ; ++z) buf[al][z][lane] = v[z];
+        }
+        __syncthreads();
+        for (int task = threadIdx.x; task < PZ * 32; task += 160) {
+            const int kz = task >> 5, ln = task & 31;
+            C io[5];
+#pragma unroll
+            for (int q = 0; q < 5; ++q) io[q] = buf[q][kz][ln];
+            block_multiply5<T>(io, sp[0][kz][ln], sp[1][kz][ln], sp[2][kz][ln], sp[3][kz][ln], sp[4][kz][ln],
+                               sp[5][kz][ln], sp[6][kz][ln]);
+#pragma unroll
+            for (int q = 0; q < 5; ++q) buf[q][kz][ln] = io[q];
+        }
+        __syncthreads();
+        C v[PZ], w[H];
+#pragma unroll
+        for (int z = 0; z < PZ; ++z) v[z] = buf[al][z][lane];
+        reg_fft_lowout<PZ, true>(v, w);
+        if (ok) {
+            const int64_t base = ((int64_t)(b * 5 + al) * nza * Py + ky) * Px + kx;
+#pragma unroll
+            for (int zi = 0; zi < H; ++zi)
+                if (zi < nza) B2[base + zi * plane] = w[zi];
         }
     }
 }

@@ -390,6 +390,9 @@ static int run_matvec(Handle* h, double omega, const double* d_omegas, int nb, c
     pa.omegas = d_omegas;
     pa.inv_P = 1.0 / ((double)Px * Py * Pz);
     pa.masked = masked;
+    pa.zcontig = 1;
+    for (int i = 1; i < nza; ++i)
+        if (h->zlist[i] != h->zlist[0] + i) pa.zcontig = 0;
 
     prof_mark(h, -1);
     // pass 3 needs the spectra: rebuild them from Tucker first when asked (Eq. 10)
