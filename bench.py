@@ -53,6 +53,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-solve", action="store_true", help="skip the whole-solve timing block")
+    p.add_argument("--with-tucker-sweep", action="store_true",
+                   help="add CR / CO of the Tucker-compressed spectra vs tolerance on plates and cubes")
     p.add_argument("--with-batch", action="store_true",
                    help="also time a graph-captured batched product over the 64 cfg-3 structures")
     return p.parse_args()
@@ -297,6 +299,10 @@ def run_batch(torch, svh, S, args):
         oms.append(2 * np.pi * it.freqs[i % 3])
     # the batch API takes one nb for all items: use the smallest port count
     nb = min(nbs)
+    t1 = time.perf_counter()
+    for h in hs:
+        h.autotune(nb)                      # FFT tile variants per grid (cached for equal grids)
+    tune_s = time.perf_counter() - t1
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     for _ in range(max(3, args.warmup)):
         b.matvec(oms, xs, ys, svh.SVH_FP32, nb=nb)
@@ -315,9 +321,56 @@ def run_batch(torch, svh, S, args):
     vox = nb * sum(kts)
     out = {"value": vox * args.steps / (tot / 1e3), "unit": UNIT, "ms_per_step": tot / args.steps,
            "structures": len(items), "nb_per_structure": nb, "sum_Kt": int(sum(kts)),
-           "launch": "one CUDA graph per step (all structures)", "setup_s": setup}
+           "launch": "one CUDA graph per step (all structures)", "setup_s": setup, "autotune_s": tune_s}
     b.close()
     for h in hs:
+        h.close()
+    return out
+
+
+def run_tucker_sweep(torch, svh, S):
+    """Compression ratio and restore overhead of the Tucker-compressed kernel
+    spectra (Sec. III.B.1, Figs. 2-3) on fully occupied plates (4 voxels thick)
+    and cubes with 1 um voxels, at tol 1e-4, 1e-6, 1e-8.
+    CR = bytes of the 7 octant spectra / bytes of their Tucker cores and factors
+    (both FP32); CO = time of the device restore of all 7 (svh_rebuild_spectra)
+    / time of one product (one right-hand side, resident spectra)."""
+    out = []
+    cases = [("plate", n, n, 4) for n in (128, 256, 512)] + [("cube", n, n, n) for n in (32, 64, 96)]
+    stream = torch.cuda.current_stream().cuda_stream
+    for kind, Kx, Ky, Kz in cases:
+        st = S.bar(Kx, Ky, Kz, 0, Kx, 0, Ky, 0, Kz, dx=1e-6)
+        h = svh.Handle(0, stream)
+        h.setup_structure(st)
+        h.generate_toeplitz()
+        info = h.info()
+        H = (info["Hx"], info["Hy"], info["Hz"])
+        full = 7 * H[0] * H[1] * H[2]
+        x = torch.from_numpy(S.random_complex(1, (1, info["N"])).astype(np.complex64)).cuda()
+        y = torch.empty_like(x)
+        om = 2 * np.pi * 1e9
+
+        def timed(fn, reps=5):
+            fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                fn()
+            e1.record()
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / reps
+
+        for tol in (1e-4, 1e-6, 1e-8):
+            ranks = h.tucker_compress(tol)
+            comp = sum(int(d1 * d2 * d3 + H[0] * d1 + H[1] * d2 + H[2] * d3) for d1, d2, d3 in ranks)
+            h.set_kernel_mode(svh.SVH_KERNELS_RESIDENT)
+            t_restore = timed(h.rebuild_spectra)
+            t_prod = timed(lambda: h.matvec(om, x, y))
+            out.append({"structure": kind, "K": [Kx, Ky, Kz], "Kt": Kx * Ky * Kz, "tol": tol,
+                        "ranks_G00": [int(v) for v in ranks[0]], "max_rank_G00": int(ranks[0].max()),
+                        "max_rank_all": int(ranks.max()), "CR": full / comp, "CO": t_restore / t_prod,
+                        "restore_ms": t_restore, "product_ms": t_prod})
         h.close()
     return out
 
@@ -341,6 +394,7 @@ def run_svh(args):
     t_setup = time.perf_counter() - t_setup
     info = h.info()
     N, nb = info["N"], args.nb
+    tiles, tile_ms = h.autotune(nb)         # FFT tile variants, timed once before the run
     Kt = info["Kx"] * info["Ky"] * info["Kz"]
     omega = 2 * np.pi * s.freqs[0]
     x = torch.from_numpy(S.random_complex(1000 + rank, (nb, N)).astype(np.complex64)).cuda()
@@ -416,15 +470,18 @@ def run_svh(args):
         solve = {"seconds": wall, "setup_s": st["setup_seconds"], "iterations": st["iterations"],
                  "refinements": st["refinements"], "final_rre": st["final_rre"],
                  "amg_avg_cg_iterations": st["amg_avg_iterations"], "L_pH": float(res["L"][0, 0, 0] * 1e12),
-                 "note": "GMRES(50), FP32 products in FP64 refinement, host AMG-FCG Schur solves (1e-8)"}
+                 "note": "GMRES(50), FP32 products in FP64 refinement, Schur solves by AMG-CG on the device (1e-8)"}
         h.set_kernel_mode(svh.SVH_KERNELS_TUCKER_REBUILD)
+    sweep = None
+    if args.with_tucker_sweep and rank == 0:
+        sweep = run_tucker_sweep(torch, svh, S)
     batch = None
     if args.with_batch and rank == 0:
         batch = run_batch(torch, svh, S, args)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(s)
-    launches_per_step = 3 + 6
+    launches_per_step = 2 + 6   # restore GEMMs (mode 3 fused into the z pass) + 6 passes
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -434,9 +491,10 @@ def run_svh(args):
                           "N": N, "nb": nb, "precision": "fp32", "kernel_spectra": "Tucker restore every step",
                           "tucker_tol": args.tucker_tol, "tucker_ranks_G00": ranks[0].tolist(),
                           "l2": "flushed before every step (512 MB write, outside the events)",
-                          "parallelism": f"replicas x{ws}", "setup_s": t_setup},
+                          "parallelism": f"replicas x{ws}", "setup_s": t_setup,
+                          "fft_tiles": {k: int(v) for k, v in zip(svh.Handle.FFT_PASSES, tiles)}},
                "fp64": fp64, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "solve": solve,
-               "batch_cfg3": batch,
+               "batch_cfg3": batch, "tucker_sweep": sweep,
                "gpu_launches": launches_per_step * args.steps, "clocks": clocks}
         print(json.dumps(out), flush=True)
     h.close()

@@ -179,7 +179,9 @@ int svh_matvec_host(svh_handle* h, double omega, int nb, const void* x, void* y,
  * GMRES(restart) with FP64 Arnoldi on the device; the preconditioner is the
  * sparse P = Q^{-1}, Q = [Y, -A^T; A, 0], Y = diag(|Z_kk|) (Eq. 12), applied
  * through the Schur complement S = A Y^{-1} A^T (Eq. 13-15) whose solves run
- * on the host by AMG-preconditioned CG to amg_tol. With inner_precision =
+ * by AMG-preconditioned CG to amg_tol: the aggregation hierarchy is built on
+ * the host once per frequency and the CG with its K-cycle runs on the device
+ * (amg_on_device = 1) or on the host cores (0). With inner_precision =
  * SVH_FP32 the Krylov products use the FP32 operator and an FP64 refinement
  * loop restores the FP64 residual. The iteration stops when every port's
  * relative residual ||b - K x|| / ||b||, measured with the FP64 operator, is
@@ -192,6 +194,7 @@ typedef struct {
     int32_t inner_precision;   /* SVH_FP32 (default) or SVH_FP64 */
     double rre;                /* relative residual target (default 1e-8, Sec. III) */
     double amg_tol;            /* relative tolerance of each Schur solve (default 1e-8, Sec. II.C) */
+    int32_t amg_on_device;     /* 1 (default): Schur solves by AMG-CG on the device; 0: on the host cores */
 } svh_options;
 
 typedef struct {
@@ -280,6 +283,24 @@ int svh_batch_solve(svh_batch* b, const double* omegas, int nfreq, const svh_opt
 #define SVH_NOALLOC_SCRATCH_BYTES (64u << 20)
 int svh_matvec_noalloc(svh_handle* h, double omega, int nb, const void* x_dev, void* y_dev, int precision);
 
+/* ---- FFT tile autotuning (batching of Sec. II.B.1 products on this GPU).
+ * The five FFT passes (0 x-forward with gather, 1 y-forward, 2 z pass,
+ * 3 y-inverse, 4 x-inverse with epilogue) have size-specialised FP32 kernels
+ * in several tile variants (radix split N1 x N2, threads per block, pruned
+ * or full z pencils). svh_autotune times every variant of every pass on this
+ * handle's grid for nb right-hand sides (zero data, 5 launches each, CUDA
+ * events on the handle's stream) and keeps the fastest for later FP32
+ * products; results are cached per process for equal grids and nb.
+ * variants[5] and ms[5] (may be NULL) receive the choices and their
+ * milliseconds per launch. svh_set_pass_variant forces one (SVH_ERR_ARG if
+ * the pass has no such variant at this size); svh_get_pass_variants reports
+ * the number of variants per pass (0: generic kernel) and the current choice.
+ * FP64 products always use variant 0. */
+#define SVH_NFFTPASS 5
+int svh_autotune(svh_handle* h, int nb, int32_t* variants, double* ms);
+int svh_set_pass_variant(svh_handle* h, int pass, int variant);
+int svh_get_pass_variants(const svh_handle* h, int32_t* counts, int32_t* chosen);
+
 /* ---- Per-pass timing of svh_matvec with CUDA events on the handle's stream.
  * Passes: 0 Tucker rebuild (Eq. 10), 1 x-forward with gather, 2 y-forward,
  * 3 z-FFT + block multiply + inverse z-FFT, 4 y-inverse, 5 x-inverse with
@@ -303,12 +324,20 @@ int svh_host_face_nodes(int Kx, int Ky, int Kz, const uint8_t* occ, int64_t* K_o
 int svh_host_spectra(int Kx, int Ky, int Kz, int Px, int Py, int Pz, const double* T, double* S);
 /* S x = b for a real symmetric positive definite CSR matrix (rowptr[n+1],
  * colidx, vals) by conjugate gradients preconditioned with the library's
- * aggregation AMG V-cycle (the inner solver of the Schur complement, Eq. 14),
+ * aggregation AMG K-cycle (the inner solver of the Schur complement, Eq. 14),
  * x0 = 0, to ||b - S x|| <= tol ||b||. iters, levels (may be NULL) receive the
  * CG iterations and the number of AMG levels. SVH_ERR_NOT_CONVERGED after
  * maxit iterations; SVH_ERR_SINGULAR if the coarsest level is not SPD. */
 int svh_host_amg_solve(int n, const int32_t* rowptr, const int32_t* colidx, const double* vals, const double* b,
                        double* x, double tol, int maxit, int32_t* iters, int32_t* levels);
+/* The same solver with the CG and its K-cycle on the current CUDA device (the
+ * hierarchy is built on the host): nrhs complex right-hand sides b[nrhs][n]
+ * (host, interleaved re, im), whose real and imaginary parts are separate real
+ * systems, each solved to ||b - S x|| <= tol ||b||; x[nrhs][n] (host) receives
+ * the solutions. iters receives the mean CG iterations per real system.
+ * Errors as svh_host_amg_solve, plus SVH_ERR_CUDA. */
+int svh_device_amg_solve(int n, const int32_t* rowptr, const int32_t* colidx, const double* vals, const double* b,
+                         double* x, int nrhs, double tol, int maxit, int32_t* iters, int32_t* levels);
 /* Algorithm 1 (Tucker-SVD) of a real D1 x D2 x D3 array O stored with the
  * mode-1 index fastest, O[(i3*D2 + i2)*D1 + i1]. The rank of mode i is the
  * smallest d_i whose discarded singular values have 2-norm <= tol/sqrt(3) *

@@ -381,6 +381,8 @@ struct Precond {
     double tol = 1e-8;
     int maxit = 500;
     long long pcg_calls = 0, pcg_iters = 0;
+    void* dev = nullptr;          // device copy of the hierarchy (amg_dev.cu)
+    ~Precond() { if (dev) amg_dev_destroy(dev); }
 };
 
 static const double kFlux[5][6] = {
@@ -528,6 +530,36 @@ int precond_schur_solve(Handle* h, int nb, int per_freq, const double* e, double
 }
 
 const double* precond_Y(Handle* h, int fi) { return P_at(h, fi)->Yd.data(); }
+int precond_nfreq(Handle* h) { return h->precond ? (int)static_cast<PrecondSet*>(h->precond)->f.size() : 0; }
+int precond_view(Handle* h, int fi, AmgView& out) {
+    if (!h->precond || fi < 0 || fi >= precond_nfreq(h)) return set_err(h, SVH_ERR_STATE, "preconditioner: not set up");
+    const Precond* P = P_at(h, fi);
+    out.lv.clear();
+    for (const AmgLevel& L : P->amg.lv) {
+        AmgLevelView v;
+        v.n = L.A.n;
+        v.nc = L.nc;
+        v.rp = L.A.rp.data();
+        v.ci = L.A.ci.data();
+        v.v = L.A.v.data();
+        v.l1 = L.l1.data();
+        v.agg = L.agg.data();
+        v.crp = L.crp.data();
+        v.cidx = L.cidx.data();
+        out.lv.push_back(v);
+    }
+    out.chol = P->amg.chol.data();
+    out.nco = P->amg.nco;
+    out.tol = P->tol;
+    out.maxit = P->maxit;
+    return SVH_OK;
+}
+void*& precond_dev(Handle* h, int fi) { return P_at(h, fi)->dev; }
+void precond_count(Handle* h, int fi, long long calls, long long iters) {
+    Precond* P = P_at(h, fi);
+    P->pcg_calls += calls;
+    P->pcg_iters += iters;
+}
 const int* precond_free_nodes(Handle* h, int* nf) {
     Precond* P = P_at(h, 0);
     *nf = (int)P->free_nodes.size();
@@ -618,4 +650,39 @@ extern "C" int svh_host_amg_solve(int n, const int32_t* rowptr, const int32_t* c
     if (iters) *iters = it;
     if (levels) *levels = (int)amg.lv.size();
     return it < 0 ? SVH_ERR_NOT_CONVERGED : SVH_OK;
+}
+
+// S x = b for nrhs complex right-hand sides (b, x: [nrhs][n] interleaved
+// re, im; real and imaginary parts are separate real systems) by the device
+// AMG-CG on a hierarchy built here (the solver of svh_solve's preconditioner).
+extern "C" int svh_device_amg_solve(int n, const int32_t* rowptr, const int32_t* colidx, const double* vals,
+                                    const double* b, double* x, int nrhs, double tol, int maxit, int32_t* iters,
+                                    int32_t* levels) {
+    if (n <= 0 || nrhs <= 0 || !rowptr || !colidx || !vals || !b || !x || !(tol > 0) || maxit <= 0) return SVH_ERR_ARG;
+    Handle h;
+    if (cudaGetDevice(&h.device) != cudaSuccess) return SVH_ERR_CUDA;
+    PrecondSet* set = new PrecondSet();
+    h.precond = set;
+    Precond* P = new Precond();
+    set->f.push_back(P);
+    P->tol = tol;
+    P->maxit = maxit;
+    P->S.n = n;
+    P->S.rp.assign(rowptr, rowptr + n + 1);
+    P->S.ci.assign(colidx, colidx + rowptr[n]);
+    P->S.v.assign(vals, vals + rowptr[n]);
+    int rc = SVH_OK;
+    DevBuf de, dx;
+    if (!amg_setup(P->S, P->amg)) rc = SVH_ERR_SINGULAR;
+    const size_t bytes = (size_t)nrhs * n * 16;
+    if (!rc) rc = dev_upload(&h, de, b, bytes);
+    if (!rc) rc = dev_alloc(&h, dx, bytes);
+    if (!rc) rc = precond_schur_solve_dev(&h, nrhs, nrhs, de.p, dx.p);
+    if (!rc && cudaMemcpy(x, dx.p, bytes, cudaMemcpyDeviceToHost) != cudaSuccess) rc = SVH_ERR_CUDA;
+    if (iters) *iters = P->pcg_calls ? (int32_t)(P->pcg_iters / P->pcg_calls) : 0;
+    if (levels) *levels = (int32_t)P->amg.lv.size();
+    dev_free(de);
+    dev_free(dx);
+    precond_free(&h);
+    return rc;
 }

@@ -1,12 +1,22 @@
 // fast_y.cu -- launchers of the size-specialised y passes (see fastpass.cuh).
+//
+// Tile variants (FP32; the autotuner times them, a.var selects one):
+//   0: the default split N = N1 x N2 with 256 threads per block,
+//   1: the same split with 512 threads (twice the kx columns per block),
+//   2: the same split with 128 threads,
+//   3: the transposed split N2 x N1 with 256 threads (sizes where both
+//      factors suit the pruned first and second stages).
+// FP64 has variant 0 only (128 threads).
+#include <type_traits>
+
 #include "fastpass.cuh"
 
 namespace svh {
 
-template <typename T, int N1, int N2, bool INV>
+template <typename T, int N1, int N2, bool INV, int NT>
 static void run_y(const PassArgs& a, cudaStream_t s) {
     using C = typename CT<T>::type;
-    constexpr int NT = sizeof(T) == 4 ? 256 : 128;
+    static_assert(NT % N2 == 0, "threads per block must be a multiple of N2");
     constexpr int TB = NT / N2;
     const size_t sm = (size_t)(N1 * N2) * (1 + TB) * sizeof(C);
     cudaFuncSetAttribute(k_ycol_fast<T, N1, N2, INV, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -14,22 +24,50 @@ static void run_y(const PassArgs& a, cudaStream_t s) {
     k_ycol_fast<T, N1, N2, INV, NT><<<grid, NT, sm, s>>>(a);
 }
 
+// N1 x N2 default split; SWAP: the transposed split is a variant too
+template <typename T, bool INV, int N1, int N2, bool SWAP>
+static bool run_y_size(const PassArgs& a, cudaStream_t s) {
+    if constexpr (std::is_same<T, float>::value) {
+        switch (a.var) {
+            case 1: run_y<T, N1, N2, INV, 512>(a, s); return true;
+            case 2: run_y<T, N1, N2, INV, 128>(a, s); return true;
+            case 3:
+                if constexpr (SWAP) { run_y<T, N2, N1, INV, 256>(a, s); return true; }
+                break;
+            default: break;
+        }
+        run_y<T, N1, N2, INV, 256>(a, s);
+    } else {
+        run_y<T, N1, N2, INV, 128>(a, s);
+    }
+    return true;
+}
+
 template <typename T, bool INV>
 static bool dispatch_y(const PassArgs& a, cudaStream_t s) {
     switch (a.Py) {
-        case 16: run_y<T, 4, 4, INV>(a, s); return true;
-        case 32: run_y<T, 8, 4, INV>(a, s); return true;
-        case 48: run_y<T, 12, 4, INV>(a, s); return true;
-        case 64: run_y<T, 8, 8, INV>(a, s); return true;
-        case 96: run_y<T, 12, 8, INV>(a, s); return true;
-        case 128: run_y<T, 16, 8, INV>(a, s); return true;
-        case 192: run_y<T, 24, 8, INV>(a, s); return true;
-        case 256: run_y<T, 16, 16, INV>(a, s); return true;
-        case 384: run_y<T, 24, 16, INV>(a, s); return true;
-        case 512: run_y<T, 32, 16, INV>(a, s); return true;
-        case 768: run_y<T, 48, 16, INV>(a, s); return true;
-        case 1024: run_y<T, 32, 32, INV>(a, s); return true;
+        case 16: return run_y_size<T, INV, 4, 4, false>(a, s);
+        case 32: return run_y_size<T, INV, 8, 4, true>(a, s);
+        case 48: return run_y_size<T, INV, 12, 4, false>(a, s);
+        case 64: return run_y_size<T, INV, 8, 8, false>(a, s);
+        case 96: return run_y_size<T, INV, 12, 8, false>(a, s);
+        case 128: return run_y_size<T, INV, 16, 8, true>(a, s);
+        case 192: return run_y_size<T, INV, 24, 8, false>(a, s);
+        case 256: return run_y_size<T, INV, 16, 16, false>(a, s);
+        case 384: return run_y_size<T, INV, 24, 16, false>(a, s);
+        case 512: return run_y_size<T, INV, 32, 16, true>(a, s);
+        case 768: return run_y_size<T, INV, 48, 16, false>(a, s);
+        case 1024: return run_y_size<T, INV, 32, 32, false>(a, s);
         default: return false;
+    }
+}
+
+int y_fast_variants(int Py, bool fp32) {
+    if (!fp32) return 1;
+    switch (Py) {
+        case 32: case 128: case 512: return 4;
+        case 16: case 48: case 64: case 96: case 192: case 256: case 384: case 768: case 1024: return 3;
+        default: return 0;
     }
 }
 

@@ -14,6 +14,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "fft_reg.cuh"
 
 namespace svh {
@@ -44,6 +46,13 @@ struct PassArgs {
     double inv_P;            // 1 / (Px Py Pz)
     int masked;
     int zcontig;             // 1 when the active planes are consecutive
+    // Tucker rebuild fused into the z pass (FP32 only): kernel u's spectra
+    // S_u[kz][ky][kx] = sum_c F3_u[kz][c] W2_u[c][ky][kx] (Eq. 10, mode 3) are
+    // formed while the pass loads them; tkW2[u] == nullptr: read spec
+    const float* tkW2[7];
+    const float* tkF3[7];
+    int tkd3[7];
+    int var;                 // tile variant of the pass being launched (0: default)
 };
 
 // outward flux of basis alpha through face f (-x,+x,-y,+y,-z,+z)
@@ -432,6 +441,56 @@ __device__ __forceinline__ void block_multiply5(typename CT<T>::type* io, T g, T
     io[0] = Yx; io[1] = Yy; io[2] = Yz; io[3] = Y2; io[4] = Y3;
 }
 
+// Spectra of one z-pass tile (32 kx columns at one ky, all PZ planes) into
+// shared memory sp[u][kz][lane], with the odd S-kernel signs folded in: only
+// the octant |k| <= P/2 is stored, so kz and PZ - kz share the value at
+// az = min(kz, PZ - kz) (Sz flips sign in the upper half, Sx/Sy by column/row).
+// One task per (kernel, column): in the fused Tucker mode its d3 mode-2 values
+// are read once and contracted with F3 for every az (same fmaf order as the
+// separate mode-3 restore, so both give identical spectra).
+template <typename T, int PZ>
+__device__ __forceinline__ void load_tile_spectra(const PassArgs& a, T (*sp)[PZ][32], int kx0, int ky) {
+    constexpr int NH = PZ / 2 + 1;
+    const T* spec = static_cast<const T*>(a.spec);
+    const int Px = a.Px, Py = a.Py;
+    const int64_t plane = (int64_t)a.Hx * a.Hy, Sk = plane * a.Hz;
+    const int ay = min(ky, Py - ky);
+    const T sgy = (2 * ky <= Py) ? (T)1 : (T)-1;
+    for (int task = threadIdx.x; task < 7 * 32; task += blockDim.x) {
+        const int u = task >> 5, ln = task & 31;
+        const int kxx = min(kx0 + ln, Px - 1);
+        const int ax = min(kxx, Px - kxx);
+        const T sgx = (2 * kxx <= Px) ? (T)1 : (T)-1;
+        const T sg = u == 1 ? sgx : (u == 2 ? sgy : (T)1);
+        const int64_t off = (int64_t)ay * a.Hx + ax;
+        T val[NH];
+        const float* W2 = std::is_same<T, float>::value ? a.tkW2[u] : nullptr;
+        if (W2) {
+            const int d3 = a.tkd3[u];
+            const float* F3 = a.tkF3[u];
+            float w[NH];
+#pragma unroll
+            for (int c = 0; c < NH; ++c) w[c] = c < d3 ? __ldg(W2 + c * plane + off) : 0.f;
+#pragma unroll
+            for (int az = 0; az < NH; ++az) {
+                float acc = 0.f;
+#pragma unroll
+                for (int c = 0; c < NH; ++c)
+                    if (c < d3) acc = fmaf(__ldg(F3 + az * d3 + c), w[c], acc);
+                val[az] = (T)acc;
+            }
+        } else {
+#pragma unroll
+            for (int az = 0; az < NH; ++az) val[az] = __ldg(spec + u * Sk + az * plane + off);
+        }
+#pragma unroll
+        for (int az = 0; az < NH; ++az) {
+            sp[u][az][ln] = sg * val[az];
+            if (az > 0 && PZ - az != az) sp[u][PZ - az][ln] = (u == 3 ? -sg : sg) * val[az];
+        }
+    }
+}
+
 // The block's spectra (7 values at each of its PZ x 32 points) are loaded once
 // into shared memory and reused for every batch item the block loops over.
 template <typename T, int PZ>
@@ -447,27 +506,7 @@ __global__ void __launch_bounds__(160) k_zpass_fast(const __grid_constant__ Pass
     const bool ok = kx < a.Px;
     const int Px = a.Px, Py = a.Py;
     // spectra of the tile, with the odd-kernel signs folded in
-    {
-        const T* spec = static_cast<const T*>(a.spec);
-        const int64_t Sk = (int64_t)a.Hx * a.Hy * a.Hz;
-        const int ay = min(ky, Py - ky);
-        const T sgy = (2 * ky <= Py) ? (T)1 : (T)-1;
-        for (int task = threadIdx.x; task < PZ * 32; task += 160) {
-            const int kz = task >> 5, ln = task & 31;
-            const int kxx = min(kx0 + ln, Px - 1);
-            const int ax = min(kxx, Px - kxx), az = min(kz, PZ - kz);
-            const T sgx = (2 * kxx <= Px) ? (T)1 : (T)-1;
-            const T sgz = (2 * kz <= PZ) ? (T)1 : (T)-1;
-            const int64_t off = ((int64_t)az * a.Hy + ay) * a.Hx + ax;
-            sp[0][kz][ln] = __ldg(spec + off);
-            sp[1][kz][ln] = sgx * __ldg(spec + Sk + off);
-            sp[2][kz][ln] = sgy * __ldg(spec + 2 * Sk + off);
-            sp[3][kz][ln] = sgz * __ldg(spec + 3 * Sk + off);
-            sp[4][kz][ln] = __ldg(spec + 4 * Sk + off);
-            sp[5][kz][ln] = __ldg(spec + 5 * Sk + off);
-            sp[6][kz][ln] = __ldg(spec + 6 * Sk + off);
-        }
-    }
+    load_tile_spectra<T, PZ>(a, sp, kx0, ky);
     C* B2 = static_cast<C*>(a.B2);
     const int64_t plane = (int64_t)Py * Px;
     // planes holding voxels: at most (Pz + 1) / 2 of them (Pz >= 2 Kz - 1)
@@ -549,27 +588,7 @@ __global__ void __launch_bounds__(160) k_zpass_half(const __grid_constant__ Pass
     const int kx = kx0 + lane;
     const bool ok = kx < a.Px;
     const int Px = a.Px, Py = a.Py;
-    {
-        const T* spec = static_cast<const T*>(a.spec);
-        const int64_t Sk = (int64_t)a.Hx * a.Hy * a.Hz;
-        const int ay = min(ky, Py - ky);
-        const T sgy = (2 * ky <= Py) ? (T)1 : (T)-1;
-        for (int task = threadIdx.x; task < PZ * 32; task += 160) {
-            const int kz = task >> 5, ln = task & 31;
-            const int kxx = min(kx0 + ln, Px - 1);
-            const int ax = min(kxx, Px - kxx), az = min(kz, PZ - kz);
-            const T sgx = (2 * kxx <= Px) ? (T)1 : (T)-1;
-            const T sgz = (2 * kz <= PZ) ? (T)1 : (T)-1;
-            const int64_t off = ((int64_t)az * a.Hy + ay) * a.Hx + ax;
-            sp[0][kz][ln] = __ldg(spec + off);
-            sp[1][kz][ln] = sgx * __ldg(spec + Sk + off);
-            sp[2][kz][ln] = sgy * __ldg(spec + 2 * Sk + off);
-            sp[3][kz][ln] = sgz * __ldg(spec + 3 * Sk + off);
-            sp[4][kz][ln] = __ldg(spec + 4 * Sk + off);
-            sp[5][kz][ln] = __ldg(spec + 5 * Sk + off);
-            sp[6][kz][ln] = __ldg(spec + 6 * Sk + off);
-        }
-    }
+    load_tile_spectra<T, PZ>(a, sp, kx0, ky);
     C* B2 = static_cast<C*>(a.B2);
     const int64_t plane = (int64_t)Py * Px;
     const int nza = a.nza;
@@ -621,5 +640,10 @@ __global__ void __launch_bounds__(160) k_zpass_half(const __grid_constant__ Pass
 template <typename T> bool launch_x_fast(const PassArgs& a, bool inv, cudaStream_t s);
 template <typename T> bool launch_y_fast(const PassArgs& a, bool inv, cudaStream_t s);
 template <typename T> bool launch_z_fast(const PassArgs& a, cudaStream_t s);
+bool z_fast_size(int Pz);
+// number of tile variants of a pass at this size (0: no specialised kernel)
+int x_fast_variants(int Px, bool inv, bool fp32);
+int y_fast_variants(int Py, bool fp32);
+int z_fast_variants(int Pz, bool fp32);
 
 }  // namespace svh

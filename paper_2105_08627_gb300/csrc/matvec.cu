@@ -20,6 +20,10 @@
 #include <algorithm>
 #include <cstdio>
 
+#include <array>
+#include <map>
+#include <mutex>
+
 #include "fastpass.cuh"
 #include "fft.cuh"
 #include "svh_internal.h"
@@ -345,6 +349,46 @@ void matvec_scratch_bytes(const Handle* h, int nb, int precision, size_t* b1, si
     *b2 = (size_t)nb * 5 * nza * (size_t)h->Py * h->Px * csz;
 }
 
+// arguments of the size-specialised pass kernels for one product
+template <typename T>
+static PassArgs pass_args(Handle* h, double omega, const double* d_omegas, int nb, const void* x, void* y, int masked,
+                          void* B1, void* B2) {
+    const int nza = (int)h->zlist.size();
+    const int nrows = (int)h->rows.size();
+    const int64_t K = h->K, M = h->M, Nvec = 5 * K + M;
+    const int Px = h->Px, Py = h->Py, Pz = h->Pz;
+    const int ti = std::is_same<T, float>::value ? 0 : 1;
+    const void* twx = ti == 0 ? h->d_tw32[0].p : h->d_tw64[0].p;
+    const void* twy = ti == 0 ? h->d_tw32[1].p : h->d_tw64[1].p;
+    const void* twz = ti == 0 ? h->d_tw32[2].p : h->d_tw64[2].p;
+    const void* spec = ti == 0 ? h->d_spec32.p : h->d_spec64.p;
+    const int32_t* vidx = static_cast<const int32_t*>(h->d_vidx.p);
+    const int32_t* rows = static_cast<const int32_t*>(h->d_rows.p);
+    const uint8_t* d_rowmask = static_cast<const uint8_t*>(h->d_rowmask.p);
+    const double mu0 = 4e-7 * 3.14159265358979323846;
+    PassArgs pa{};
+    pa.x = x; pa.y = y; pa.B1 = B1; pa.B2 = B2; pa.spec = spec;
+    pa.twx = twx; pa.twy = twy; pa.twz = twz;
+    pa.vidx = vidx; pa.rows = rows; pa.rowmask = d_rowmask;
+    pa.zlist = static_cast<const int32_t*>(h->d_zlist.p);
+    pa.node = static_cast<const int32_t*>(h->d_node.p);
+    pa.freem = static_cast<const uint8_t*>(h->d_free.p);
+    pa.lam = static_cast<const double*>(h->d_lam.p);
+    pa.sig0 = static_cast<const double*>(h->d_sig0.p);
+    pa.K = K; pa.M = M; pa.Nvec = Nvec; pa.nlines = (int64_t)nb * 5 * nrows;
+    pa.nb = nb; pa.nza = nza; pa.nrows = nrows; pa.Kx = h->Kx; pa.Ky = h->Ky; pa.Kz = h->Kz;
+    pa.Px = Px; pa.Py = Py; pa.Pz = Pz; pa.Hx = h->Hx; pa.Hy = h->Hy; pa.Hz = h->Hz;
+    pa.omega = omega; pa.mu = mu0; pa.dx = h->dx;
+    pa.conv_scale = omega * mu0 * h->dx / ((double)Px * Py * Pz);
+    pa.omegas = d_omegas;
+    pa.inv_P = 1.0 / ((double)Px * Py * Pz);
+    pa.masked = masked;
+    pa.zcontig = 1;
+    for (int i = 1; i < nza; ++i)
+        if (h->zlist[i] != h->zlist[0] + i) pa.zcontig = 0;
+    return pa;
+}
+
 // The launch sequence on caller-provided intermediate grids B1, B2.
 template <typename T>
 static int run_matvec(Handle* h, double omega, const double* d_omegas, int nb, const void* xv, void* yv, int masked,
@@ -372,36 +416,28 @@ static int run_matvec(Handle* h, double omega, const double* d_omegas, int nb, c
     const int32_t* vidx = static_cast<const int32_t*>(h->d_vidx.p);
     const int32_t* rows = static_cast<const int32_t*>(h->d_rows.p);
     const uint8_t* d_rowmask = static_cast<const uint8_t*>(h->d_rowmask.p);
-    const double mu0 = 4e-7 * 3.14159265358979323846;
-    PassArgs pa{};
-    pa.x = x; pa.y = y; pa.B1 = B1; pa.B2 = B2; pa.spec = spec;
-    pa.twx = twx; pa.twy = twy; pa.twz = twz;
-    pa.vidx = vidx; pa.rows = rows; pa.rowmask = d_rowmask;
-    pa.zlist = static_cast<const int32_t*>(h->d_zlist.p);
-    pa.node = static_cast<const int32_t*>(h->d_node.p);
-    pa.freem = static_cast<const uint8_t*>(h->d_free.p);
-    pa.lam = static_cast<const double*>(h->d_lam.p);
-    pa.sig0 = static_cast<const double*>(h->d_sig0.p);
-    pa.K = K; pa.M = M; pa.Nvec = Nvec; pa.nlines = (int64_t)nb * 5 * nrows;
-    pa.nb = nb; pa.nza = nza; pa.nrows = nrows; pa.Kx = h->Kx; pa.Ky = h->Ky; pa.Kz = h->Kz;
-    pa.Px = Px; pa.Py = Py; pa.Pz = Pz; pa.Hx = h->Hx; pa.Hy = h->Hy; pa.Hz = h->Hz;
-    pa.omega = omega; pa.mu = mu0; pa.dx = h->dx;
-    pa.conv_scale = omega * mu0 * h->dx / ((double)Px * Py * Pz);
-    pa.omegas = d_omegas;
-    pa.inv_P = 1.0 / ((double)Px * Py * Pz);
-    pa.masked = masked;
-    pa.zcontig = 1;
-    for (int i = 1; i < nza; ++i)
-        if (h->zlist[i] != h->zlist[0] + i) pa.zcontig = 0;
-
+    PassArgs pa = pass_args<T>(h, omega, d_omegas, nb, x, y, masked, B1, B2);
     prof_mark(h, -1);
     // pass 3 needs the spectra: rebuild them from Tucker first when asked (Eq. 10)
     if (allow_rebuild && ti == 0 && h->kernel_mode == SVH_KERNELS_TUCKER_REBUILD) {
-        int rc = launch_tucker_rebuild(h);
+        // every kernel has Tucker data in this mode; the size-specialised z
+        // pass takes the last mode product itself
+        bool fused = z_fast_size(Pz);
+        for (int u = 0; u < 7; ++u) fused = fused && h->tucker_on[u];
+        TuckerFuse tf{};
+        int rc = launch_tucker_rebuild(h, fused ? &tf : nullptr);
         if (rc) return rc;
+        if (fused)
+            for (int u = 0; u < 7; ++u) {
+                pa.tkW2[u] = tf.W2[u];
+                pa.tkF3[u] = tf.F3[u];
+                pa.tkd3[u] = tf.d3[u];
+            }
     }
     prof_mark(h, 0);
+    auto var = [&](int p) { return ti == 0 ? h->tune32[p] : 0; };
     // pass 1
+    pa.var = var(0);
     if (!launch_x_fast<T>(pa, false, h->stream)) {
         int lpb = std::max(1, MAXPTS * NTHR / Px);
         int64_t nlines = (int64_t)nb * 5 * nrows;
@@ -414,6 +450,7 @@ static int run_matvec(Handle* h, double omega, const double* d_omegas, int nb, c
     prof_mark(h, 1);
     // pass 2
     int tby = std::max(1, std::min(32, MAXPTS * NTHR / Py));
+    pa.var = var(1);
     if (!launch_y_fast<T>(pa, false, h->stream)) {
         size_t sm = (size_t)(Py + Py * tby) * csz;
         cudaFuncSetAttribute(k_ycol<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -422,6 +459,7 @@ static int run_matvec(Handle* h, double omega, const double* d_omegas, int nb, c
     }
     prof_mark(h, 2);
     // pass 3
+    pa.var = var(2);
     if (!launch_z_fast<T>(pa, h->stream)) {
         int tbz = std::max(1, std::min(64, MAXPTS * NTHR / (5 * Pz)));
         size_t sm = (size_t)(Pz + Pz * 5 * tbz) * csz;
@@ -432,6 +470,7 @@ static int run_matvec(Handle* h, double omega, const double* d_omegas, int nb, c
     }
     prof_mark(h, 3);
     // pass 4
+    pa.var = var(3);
     if (!launch_y_fast<T>(pa, true, h->stream)) {
         size_t sm = (size_t)(Py + Py * tby) * csz;
         cudaFuncSetAttribute(k_ycol<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -440,6 +479,7 @@ static int run_matvec(Handle* h, double omega, const double* d_omegas, int nb, c
     }
     prof_mark(h, 4);
     // pass 5 + epilogue
+    pa.var = var(4);
     if (!launch_x_fast<T>(pa, true, h->stream)) {
         int lpb = std::max(1, MAXPTS * NTHR / Px);
         int64_t nlines = (int64_t)nb * 5 * nrows;
@@ -487,6 +527,112 @@ int launch_matvec64(Handle* h, double omega, int nb, const void* x, void* y, int
 int launch_matvec_on(Handle* h, double omega, int nb, const void* x, void* y, int precision, void* B1, void* B2) {
     return precision == SVH_FP32 ? run_matvec<float>(h, omega, nullptr, nb, x, y, 0, B1, B2, false)
                                  : run_matvec<double>(h, omega, nullptr, nb, x, y, 0, B1, B2, false);
+}
+
+// ---- FFT tile autotuning
+static int pass_variants(const Handle* h, int p) {
+    switch (p) {
+        case 0: return x_fast_variants(h->Px, false, true);
+        case 1: return y_fast_variants(h->Py, true);
+        case 2: return z_fast_variants(h->Pz, true);
+        case 3: return y_fast_variants(h->Py, true);
+        default: return x_fast_variants(h->Px, true, true);
+    }
+}
+
+static bool launch_pass(const PassArgs& a, int p, cudaStream_t s) {
+    switch (p) {
+        case 0: return launch_x_fast<float>(a, false, s);
+        case 1: return launch_y_fast<float>(a, false, s);
+        case 2: return launch_z_fast<float>(a, s);
+        case 3: return launch_y_fast<float>(a, true, s);
+        default: return launch_x_fast<float>(a, true, s);
+    }
+}
+
+struct TuneKey {
+    int v[9];
+    bool operator<(const TuneKey& o) const { return std::lexicographical_compare(v, v + 9, o.v, o.v + 9); }
+};
+static std::mutex g_tune_mu;
+static std::map<TuneKey, std::array<int, 5>> g_tune_cache;
+
+int autotune(Handle* h, int nb, int32_t* variants, double* ms) {
+    const TuneKey key{{h->Px, h->Py, h->Pz, (int)h->zlist.size(), (int)h->rows.size(), h->Kx, h->Ky, h->Kz, nb}};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end() && !ms) {
+            for (int p = 0; p < 5; ++p) {
+                h->tune32[p] = it->second[p];
+                if (variants) variants[p] = it->second[p];
+            }
+            return SVH_OK;
+        }
+    }
+    size_t b1, b2;
+    matvec_scratch_bytes(h, nb, SVH_FP32, &b1, &b2);
+    if (h->d_B1.bytes < b1) { int rc = dev_alloc(h, h->d_B1, b1); if (rc) return rc; }
+    if (h->d_B2.bytes < b2) { int rc = dev_alloc(h, h->d_B2, b2); if (rc) return rc; }
+    const size_t vb = (size_t)nb * (5 * h->K + h->M) * 8;
+    DevBuf x, y;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = SVH_OK;
+    auto done = [&](int r) {
+        dev_free(x);
+        dev_free(y);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        return r;
+    };
+    if ((rc = dev_alloc(h, x, vb)) || (rc = dev_alloc(h, y, vb))) return done(rc);
+    cudaStream_t s = h->stream;
+    if (cudaMemsetAsync(x.p, 0, vb, s) != cudaSuccess || cudaMemsetAsync(h->d_B1.p, 0, b1, s) != cudaSuccess ||
+        cudaMemsetAsync(h->d_B2.p, 0, b2, s) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+        cudaEventCreate(&e1) != cudaSuccess)
+        return done(set_err(h, SVH_ERR_CUDA, "svh_autotune: CUDA set-up failed"));
+    PassArgs pa = pass_args<float>(h, 2e9 * 3.14159265358979323846, nullptr, nb, x.p, y.p, 0, h->d_B1.p, h->d_B2.p);
+    std::array<int, 5> best{};
+    constexpr int REPS = 5;
+    for (int p = 0; p < 5; ++p) {
+        const int nv = pass_variants(h, p);
+        double tbest = -1;
+        best[p] = 0;
+        for (int v = 0; v < nv; ++v) {
+            pa.var = v;
+            launch_pass(pa, p, s);   // warm-up (and the shared-memory attribute)
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < REPS; ++r) launch_pass(pa, p, s);
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) return done(set_err(h, SVH_ERR_CUDA, "svh_autotune: launch failed"));
+            float t = 0;
+            cudaEventElapsedTime(&t, e0, e1);
+            if (cudaGetLastError() != cudaSuccess) return done(set_err(h, SVH_ERR_CUDA, "svh_autotune: launch failed"));
+            if (tbest < 0 || t < tbest) { tbest = t; best[p] = v; }
+        }
+        h->tune32[p] = best[p];
+        if (variants) variants[p] = best[p];
+        if (ms) ms[p] = tbest < 0 ? 0.0 : tbest / REPS;
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = best;
+    }
+    return done(SVH_OK);
+}
+
+int set_pass_variant(Handle* h, int pass, int variant) {
+    if (pass < 0 || pass >= 5 || variant < 0 || variant >= std::max(1, pass_variants(h, pass)))
+        return set_err(h, SVH_ERR_ARG, "svh_set_pass_variant: no such pass or variant at this size");
+    h->tune32[pass] = variant;
+    return SVH_OK;
+}
+
+void get_pass_variants(const Handle* h, int32_t* counts, int32_t* chosen) {
+    for (int p = 0; p < 5; ++p) {
+        if (counts) counts[p] = pass_variants(h, p);
+        if (chosen) chosen[p] = h->tune32[p];
+    }
 }
 
 }  // namespace svh

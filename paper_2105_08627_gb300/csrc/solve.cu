@@ -235,6 +235,7 @@ __global__ void k_prec_post_node(const double2* __restrict__ v, double2* __restr
 struct SolveWork {
     int nb = 0, m = 0;
     int per_freq = 1;        // items of one frequency (= number of ports)
+    int amg_dev = 1;         // Schur solves on the device
     int64_t N = 0;
     int nf = 0;
     DevBuf X, B, R, W, D, V, Z, T32a, T32b, part, hbuf, E, Bs, Yd, freeid, freenodes, scl, om;
@@ -295,12 +296,16 @@ static int apply_precond(Handle* h, SolveWork& s, const double2* in, double2* ou
                                                                      static_cast<int32_t*>(s.freenodes.p), nf,
                                                                      static_cast<int32_t*>(h->d_ninc.p),
                                                                      static_cast<double2*>(s.E.p));
-    std::vector<double> e((size_t)s.nb * nf * 2), b((size_t)s.nb * nf * 2);
-    SVH_CUDA_TRY(h, cudaMemcpyAsync(e.data(), s.E.p, e.size() * 8, cudaMemcpyDeviceToHost, h->stream));
-    SVH_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
-    int rc = precond_schur_solve(h, s.nb, s.per_freq, e.data(), b.data());
-    if (rc) return rc;
-    SVH_CUDA_TRY(h, cudaMemcpyAsync(s.Bs.p, b.data(), b.size() * 8, cudaMemcpyHostToDevice, h->stream));
+    if (s.amg_dev) {
+        if (int rc = precond_schur_solve_dev(h, s.nb, s.per_freq, s.E.p, s.Bs.p)) return rc;
+    } else {
+        std::vector<double> e((size_t)s.nb * nf * 2), b((size_t)s.nb * nf * 2);
+        SVH_CUDA_TRY(h, cudaMemcpyAsync(e.data(), s.E.p, e.size() * 8, cudaMemcpyDeviceToHost, h->stream));
+        SVH_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+        int rc = precond_schur_solve(h, s.nb, s.per_freq, e.data(), b.data());
+        if (rc) return rc;
+        SVH_CUDA_TRY(h, cudaMemcpyAsync(s.Bs.p, b.data(), b.size() * 8, cudaMemcpyHostToDevice, h->stream));
+    }
     k_prec_post_vox<<<dim3(blocks_for(5 * K), s.nb), 256, 0, h->stream>>>(
         in, out, N, K, static_cast<double*>(s.Yd.p), s.per_freq, static_cast<int32_t*>(h->d_node.p),
         static_cast<int32_t*>(s.freeid.p), static_cast<double2*>(s.Bs.p), nf);
@@ -469,6 +474,7 @@ void svh_default_options(svh_options* o) {
     o->inner_precision = SVH_FP32;
     o->rre = 1e-8;
     o->amg_tol = 1e-8;
+    o->amg_on_device = 1;
 }
 
 int svh_solve(svh_handle* hh, const double* omegas, int nfreq, const svh_options* opt_in, double* Zport,
@@ -485,7 +491,8 @@ int svh_solve(svh_handle* hh, const double* omegas, int nfreq, const svh_options
     svh_default_options(&opt);
     if (opt_in) opt = *opt_in;
     if (opt.restart < 1 || opt.restart > 500 || !(opt.rre > 0) || !(opt.amg_tol > 0) || opt.max_iterations < 1 ||
-        opt.max_refinements < 1 || (opt.inner_precision != SVH_FP32 && opt.inner_precision != SVH_FP64))
+        opt.max_refinements < 1 || (opt.inner_precision != SVH_FP32 && opt.inner_precision != SVH_FP64) ||
+        (opt.amg_on_device != 0 && opt.amg_on_device != 1))
         return set_err(h, SVH_ERR_ARG, "svh_solve: bad options");
     for (int f = 0; f < nfreq; ++f)
         if (!(omegas[f] > 0) || !std::isfinite(omegas[f])) return set_err(h, SVH_ERR_ARG, "svh_solve: omega must be > 0");
@@ -495,6 +502,7 @@ int svh_solve(svh_handle* hh, const double* omegas, int nfreq, const svh_options
     const int nb = np * nfreq;
     SolveWork s;
     s.per_freq = np;
+    s.amg_dev = opt.amg_on_device;
     int rc = alloc_work(h, s, nb, opt.restart);
     if (rc) return rc;
     // right-hand sides: b_I = A_T^T Phi_T with Phi = 1 on the plus nodes of port p (same at every frequency)

@@ -795,6 +795,29 @@ int svh_matvec(svh_handle* hh, double omega, int nb, const void* x, void* y, int
     return precision == SVH_FP32 ? launch_matvec32(h, omega, nb, x, y, 0) : launch_matvec64(h, omega, nb, x, y, 0);
 }
 
+int svh_autotune(svh_handle* hh, int nb, int32_t* variants, double* ms) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    HCHECK(h);
+    if (!h->have_grid || !h->have_kernels) return set_err(h, SVH_ERR_STATE, "svh_autotune: grid and kernels needed");
+    if (nb <= 0) return set_err(h, SVH_ERR_ARG, "svh_autotune: nb must be positive");
+    return autotune(h, nb, variants, ms);
+}
+
+int svh_set_pass_variant(svh_handle* hh, int pass, int variant) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h) return SVH_ERR_ARG;
+    if (!h->have_grid) return set_err(h, SVH_ERR_STATE, "svh_set_pass_variant: no grid");
+    return set_pass_variant(h, pass, variant);
+}
+
+int svh_get_pass_variants(const svh_handle* hh, int32_t* counts, int32_t* chosen) {
+    const Handle* h = reinterpret_cast<const Handle*>(hh);
+    if (!h) return SVH_ERR_ARG;
+    if (!h->have_grid) return SVH_ERR_STATE;
+    get_pass_variants(h, counts, chosen);
+    return SVH_OK;
+}
+
 int svh_matvec_omegas(svh_handle* hh, const double* omegas, int nb, const void* x, void* y, int precision) {
     Handle* h = reinterpret_cast<Handle*>(hh);
     HCHECK(h);

@@ -90,6 +90,7 @@ struct Handle {
     DevBuf d_B1, d_B2;
     DevBuf d_xin, d_yout;              // staging for svh_matvec_host
     DevBuf d_omegas;                   // per-item frequencies for svh_matvec_omegas
+    int tune32[5] = {0, 0, 0, 0, 0};   // FP32 tile variant per FFT pass (svh_autotune)
 };
 
 int set_err(Handle* h, int code, const std::string& msg);
@@ -109,6 +110,10 @@ int launch_matvec64(Handle* h, double omega, int nb, const void* x, void* y, int
 // same product on caller-provided intermediate grids (no allocation, no Tucker restore)
 int launch_matvec_on(Handle* h, double omega, int nb, const void* x, void* y, int precision, void* B1, void* B2);
 void matvec_scratch_bytes(const Handle* h, int nb, int precision, size_t* b1, size_t* b2);
+// FFT tile variants (matvec.cu)
+int autotune(Handle* h, int nb, int32_t* variants, double* ms);
+int set_pass_variant(Handle* h, int pass, int variant);
+void get_pass_variants(const Handle* h, int32_t* counts, int32_t* chosen);
 // quadrature of the unit kernels (kernels_gen.cu): fills T[7][Kz][Ky][Kx] (host)
 int generate_toeplitz_device(Handle* h, std::vector<double>& T);
 // sparse preconditioner (amg.cpp)
@@ -120,8 +125,38 @@ const int* precond_free_nodes(Handle* h, int* nf);
 int precond_levels(Handle* h);
 double precond_avg_iters(Handle* h);
 int precond_apply_host(Handle* h, int nb, const double* in, double* out);
+// read-only view of frequency fi's AMG hierarchy (amg.cpp) for the device solver
+struct AmgLevelView {
+    int n = 0, nc = 0;
+    const int *rp = nullptr, *ci = nullptr;
+    const double *v = nullptr, *l1 = nullptr;
+    const int *agg = nullptr, *crp = nullptr, *cidx = nullptr;
+};
+struct AmgView {
+    std::vector<AmgLevelView> lv;
+    const double* chol = nullptr;   // coarsest Cholesky factor, row-major lower, nco x nco
+    int nco = 0;
+    double tol = 1e-8;
+    int maxit = 500;
+};
+int precond_nfreq(Handle* h);
+int precond_view(Handle* h, int fi, AmgView& out);
+// device copy of frequency fi's hierarchy, owned by the preconditioner (amg_dev.cu)
+void*& precond_dev(Handle* h, int fi);
+void precond_count(Handle* h, int fi, long long calls, long long iters);
+void amg_dev_destroy(void* d);
+// b = S^{-1} e on the device; e, b: double2 [nb][nf] device arrays
+int precond_schur_solve_dev(Handle* h, int nb, int per_freq, const void* e_dev, void* b_dev);
 // Tucker rebuild (tucker.cu)
-int launch_tucker_rebuild(Handle* h);
+// restore the FP32 spectra from Tucker data (Eq. 10); with fuse != nullptr
+// the last mode product is left to the z pass: fuse receives, per kernel, the
+// mode-2 result W2[c][Hy][Hx], the factor F3[Hz][d3] and d3
+struct TuckerFuse {
+    const float* W2[7];
+    const float* F3[7];
+    int d3[7];
+};
+int launch_tucker_rebuild(Handle* h, TuckerFuse* fuse = nullptr);
 
 }  // namespace svh
 

@@ -176,7 +176,43 @@ __global__ void __launch_bounds__(256) k_mode3(const __grid_constant__ Mode3 a) 
     }
 }
 
-int launch_tucker_rebuild(Handle* h) {
+// k_mode3 with the plane count a compile-time constant (Hz = Pz / 2 + 1 of
+// the specialised z sizes): d3 <= Hz values per point in registers, no
+// shared memory, the same fmaf order as k_mode3 and the fused z pass.
+template <int NH>
+__global__ void __launch_bounds__(256) k_mode3_h(const __grid_constant__ Mode3 a) {
+    const int s = blockIdx.y;
+    const int64_t n = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (n >= a.n) return;
+    const int d3 = a.d3[s];
+    const float* F3 = a.F3[s];
+    float w[NH];
+#pragma unroll
+    for (int c = 0; c < NH; ++c) w[c] = c < d3 ? __ldg(a.W2[s] + (int64_t)c * a.n + n) : 0.f;
+#pragma unroll
+    for (int kz = 0; kz < NH; ++kz) {
+        float acc = 0.f;
+#pragma unroll
+        for (int c = 0; c < NH; ++c)
+            if (c < d3) acc = fmaf(__ldg(F3 + kz * d3 + c), w[c], acc);
+        a.out[s][(int64_t)kz * a.n + n] = acc;
+    }
+}
+
+static bool launch_mode3_h(const Mode3& m3, int nz, cudaStream_t st) {
+    const dim3 grid((unsigned)((m3.n + 255) / 256), nz);
+    switch (m3.Hz) {
+        case 5: k_mode3_h<5><<<grid, 256, 0, st>>>(m3); return true;
+        case 7: k_mode3_h<7><<<grid, 256, 0, st>>>(m3); return true;
+        case 9: k_mode3_h<9><<<grid, 256, 0, st>>>(m3); return true;
+        case 13: k_mode3_h<13><<<grid, 256, 0, st>>>(m3); return true;
+        case 17: k_mode3_h<17><<<grid, 256, 0, st>>>(m3); return true;
+        case 25: k_mode3_h<25><<<grid, 256, 0, st>>>(m3); return true;
+        default: return false;
+    }
+}
+
+int launch_tucker_rebuild(Handle* h, TuckerFuse* fuse) {
     const int Hx = h->Hx, Hy = h->Hy, Hz = h->Hz;
     const int64_t Ht = (int64_t)Hx * Hy * Hz;
     size_t n1 = 0, n2 = 0;
@@ -243,6 +279,15 @@ int launch_tucker_rebuild(Handle* h) {
     }
     // mode 3
     const int nz = h->tk_probs_split[2];
+    if (fuse) {
+        for (int i = 0; i < nz && i < 7; ++i) {
+            fuse->W2[i] = all[off + i].B;
+            fuse->F3[i] = all[off + i].A;
+            fuse->d3[i] = all[off + i].K;
+        }
+        SVH_CUDA_TRY(h, cudaGetLastError());
+        return SVH_OK;
+    }
     bool small = Hz <= 64;
     for (int i = 0; i < nz; ++i) small = small && all[off + i].K <= 64;
     if (small && nz) {
@@ -255,7 +300,8 @@ int launch_tucker_rebuild(Handle* h) {
         }
         m3.n = (int64_t)Hy * Hx;
         m3.Hz = Hz;
-        k_mode3<<<dim3((unsigned)((m3.n + 255) / 256), nz), 256, 0, h->stream>>>(m3);
+        if (!launch_mode3_h(m3, nz, h->stream))
+            k_mode3<<<dim3((unsigned)((m3.n + 255) / 256), nz), 256, 0, h->stream>>>(m3);
     } else if (nz) {
         int mt = 0, nt = 0;
         for (int i = 0; i < nz; ++i) {

@@ -44,7 +44,8 @@ class svh_port(C.Structure):
 
 class svh_options(C.Structure):
     _fields_ = [("restart", C.c_int32), ("max_iterations", C.c_int32), ("max_refinements", C.c_int32),
-                ("inner_precision", C.c_int32), ("rre", C.c_double), ("amg_tol", C.c_double)]
+                ("inner_precision", C.c_int32), ("rre", C.c_double), ("amg_tol", C.c_double),
+                ("amg_on_device", C.c_int32)]
 
 
 class svh_stats(C.Structure):
@@ -111,10 +112,15 @@ SIGNATURES = {
     "svh_batch_solve": (C.c_int, [_P, _DP, C.c_int, C.POINTER(svh_options), C.POINTER(_DP), C.c_int,
                                   C.POINTER(svh_stats)]),
     "svh_profile_begin": (C.c_int, [_P, C.c_int]),
+    "svh_autotune": (C.c_int, [_P, C.c_int, _I32P, _DP]),
+    "svh_set_pass_variant": (C.c_int, [_P, C.c_int, C.c_int]),
+    "svh_get_pass_variants": (C.c_int, [_P, _I32P, _I32P]),
     "svh_profile_end": (C.c_int, [_P, _DP, _I32P]),
     "svh_host_face_nodes": (C.c_int, [C.c_int, C.c_int, C.c_int, _U8P, _I64P, _I64P, _I32P]),
     "svh_host_spectra": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _DP, _DP]),
     "svh_host_amg_solve": (C.c_int, [C.c_int, _I32P, _I32P, _DP, _DP, _DP, C.c_double, C.c_int, _I32P, _I32P]),
+    "svh_device_amg_solve": (C.c_int, [C.c_int, _I32P, _I32P, _DP, _DP, _DP, C.c_int, C.c_double, C.c_int, _I32P,
+                                        _I32P]),
     "svh_host_tucker_svd": (C.c_int, [_DP, C.c_int, C.c_int, C.c_int, C.c_double, _I32P, _DP, _DP, _DP, _DP]),
 }
 
@@ -186,6 +192,25 @@ def host_amg_solve(S, b, tol=1e-8, maxit=500):
     _check_host(lib().svh_host_amg_solve(S.shape[0], _i32p(rp), _i32p(ci), _dp(v), _dp(b), _dp(x), tol, maxit,
                                          C.byref(it), C.byref(lv)), "svh_host_amg_solve")
     return x, it.value, lv.value
+
+
+def device_amg_solve(S, b, tol=1e-8, maxit=500):
+    """x = S^-1 b by the device AMG-CG (S: scipy CSR, SPD; b: complex [nrhs, n] or [n];
+    real and imaginary parts are separate systems) -> (x, mean iterations, levels)."""
+    S = S.tocsr()
+    rp = np.ascontiguousarray(S.indptr, np.int32)
+    ci = np.ascontiguousarray(S.indices, np.int32)
+    v = np.ascontiguousarray(S.data, np.float64)
+    b = np.asarray(b, np.complex128)
+    shape = b.shape
+    b2 = np.ascontiguousarray(b.reshape(-1, S.shape[0]))
+    x = np.zeros_like(b2)
+    it = C.c_int32()
+    lv = C.c_int32()
+    _check_host(lib().svh_device_amg_solve(S.shape[0], _i32p(rp), _i32p(ci), _dp(v), _dp(b2.view(np.float64)),
+                                           _dp(x.view(np.float64)), b2.shape[0], tol, maxit, C.byref(it),
+                                           C.byref(lv)), "svh_device_amg_solve")
+    return x.reshape(shape), it.value, lv.value
 
 
 def host_tucker_svd(O, tol):
@@ -350,7 +375,7 @@ class Handle:
         """Port impedances at the given frequencies (Hz) -> dict(Z[f,p,q], L = Im Z / omega, R, stats).
 
         opts override svh_options fields (restart, max_iterations, max_refinements,
-        inner_precision, rre, amg_tol). Raises SVHError on failure; a solve that
+        inner_precision, rre, amg_tol, amg_on_device). Raises SVHError on failure; a solve that
         stops above rre raises with code SVH_ERR_NOT_CONVERGED unless
         allow_unconverged=True."""
         allow = opts.pop("allow_unconverged", False)
@@ -403,6 +428,26 @@ class Handle:
         return out
 
     PASSES = ("tucker_rebuild", "x_fwd", "y_fwd", "z_pass", "y_inv", "x_inv_epilogue", "node_rows")
+
+    FFT_PASSES = ("x_fwd", "y_fwd", "z_pass", "y_inv", "x_inv_epilogue")
+
+    def autotune(self, nb):
+        """Time every FP32 tile variant of the five FFT passes for nb items and keep
+        the fastest -> (variants[5], ms per launch[5])."""
+        v = np.zeros(5, np.int32)
+        ms = np.zeros(5)
+        self._ck(lib().svh_autotune(self._h, int(nb), _i32p(v), _dp(ms)), "svh_autotune")
+        return v, ms
+
+    def set_pass_variant(self, p, v):
+        self._ck(lib().svh_set_pass_variant(self._h, int(p), int(v)), "svh_set_pass_variant")
+
+    def pass_variants(self):
+        """-> (number of variants per FFT pass (0: generic kernel), current choice)."""
+        n = np.zeros(5, np.int32)
+        c = np.zeros(5, np.int32)
+        self._ck(lib().svh_get_pass_variants(self._h, _i32p(n), _i32p(c)), "svh_get_pass_variants")
+        return n, c
 
     def profile_begin(self, max_calls):
         self._ck(lib().svh_profile_begin(self._h, int(max_calls)), "svh_profile_begin")

@@ -251,3 +251,35 @@ def test_esfq_512x512x24_sampled_rows():
         got = np.concatenate([np.stack([y[b * g.K + rows] for b in range(5)]).ravel(), y[5 * g.K + nodes]])
         assert np.abs(got - ref).max() <= tol * np.abs(ref).max(), (dt, np.abs(got - ref).max() / np.abs(ref).max())
     h.close()
+
+
+@pytest.mark.parametrize("seed,shape", [
+    (61, (64, 16, 8)),     # P = 128, 32, 16: transposed-split variants on x and y
+    (62, (48, 24, 12)),    # P = 96, 48, 24: x inverse without a grouped kernel
+])
+def test_every_tile_variant_and_autotune(seed, shape):
+    """a12: each FFT tile variant the autotuner may pick gives the oracle's product."""
+    torch = _torch()
+    s = S.random_blob(seed, *shape, fill=0.5)
+    g, S7, Pr, T = oracle_reference(s)
+    om = 2 * np.pi * 2e9
+    nb = 3
+    x = S.random_complex(seed, (nb, g.N))
+    yref = np.stack([op.apply_K_fft(g, S7, x[b], om, Pr) for b in range(nb)])
+    h = handle_for(s, toeplitz=T)
+    xd = torch.from_numpy(x.astype(np.complex64)).cuda()
+    counts, chosen = h.pass_variants()
+    assert np.all(counts >= 2) and np.all(chosen == 0)
+    for p in range(5):
+        for v in range(counts[p]):
+            h.set_pass_variant(p, v)
+            y = h.matvec(om, xd).cpu().numpy().astype(np.complex128)
+            _check_fp32(y, yref)
+        h.set_pass_variant(p, 0)
+    with pytest.raises(Exception):
+        h.set_pass_variant(0, counts[0])
+    v, ms = h.autotune(nb)
+    assert np.all((v >= 0) & (v < counts)) and np.all(ms > 0)
+    assert np.array_equal(h.pass_variants()[1], v)
+    _check_fp32(h.matvec(om, xd).cpu().numpy().astype(np.complex128), yref)
+    h.close()

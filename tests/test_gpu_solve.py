@@ -127,3 +127,56 @@ def test_meander_256x256x8_solve_true_residual():
     assert rel <= 2e-8, rel
     assert res["L"][0, 0, 0] > 0
     h.close()
+
+
+def _schur(s, seed):
+    """S = A_F diag(1/y) A_F^T on the free nodes of a structure (the Eq. 14
+    operator), y_beta = s_beta (Eq. 16-18 scale) times a seeded factor within
+    half a decade either way."""
+    import scipy.sparse as sp
+    g = G.build_grid(s)
+    free = np.flatnonzero(~G.terminal_nodes(g))
+    AF = g.A[free].tocsr()
+    y = np.repeat([1, 1, 1, 1 / 6, 1 / 2], g.K) * 10.0 ** np.random.default_rng(seed).uniform(-0.5, 0.5, 5 * g.K)
+    return (AF @ sp.diags(1.0 / y) @ AF.T).tocsr()
+
+
+@pytest.mark.parametrize("item", [0, 2])
+def test_device_amg_matches_direct_solve(item):
+    """Device AMG-CG (several complex right-hand sides = pairs of real systems)
+    against a sparse direct solve and the host AMG-CG on the same operator.
+    Each real system stops at ||r|| <= tol ||b||, so ||x - x*|| <= ||r|| / lambda_min(S)."""
+    import scipy.sparse.linalg as spla
+    from paper_2105_08627_gb300 import svh
+    s = S.batch_cfg3(seed=303, n_items=6)[item]
+    Sm = _schur(s, 5)
+    n = Sm.shape[0]
+    tol = 1e-10
+    b = S.random_complex(6, (3, n))
+    b[1].imag = 0.0                       # a system with a zero right-hand side stays zero
+    x, it, lv = svh.device_amg_solve(Sm, b, tol=tol)
+    assert lv >= 2 and it > 0
+    lu = spla.splu(Sm.tocsc())
+    lam_min = spla.eigsh(Sm, k=1, sigma=0, which="LM", return_eigenvectors=False)[0]
+    assert lam_min > 0
+    for r in range(3):
+        ref = lu.solve(b[r].real) + 1j * lu.solve(b[r].imag)
+        res = np.linalg.norm(Sm @ x[r] - b[r])
+        assert res <= 2 * tol * np.linalg.norm(b[r]), (r, res / np.linalg.norm(b[r]))
+        assert np.linalg.norm(x[r] - ref) <= 1.01 * res / lam_min + 1e-14 * np.linalg.norm(ref)
+    assert np.all(x[1].imag == 0.0)
+    xh, ith, lvh = svh.host_amg_solve(Sm, b[0].real, tol=tol)
+    assert lvh == lv
+    rh = np.linalg.norm(Sm @ xh - b[0].real)
+    rd = np.linalg.norm(Sm @ x[0].real - b[0].real)
+    assert np.linalg.norm(xh - x[0].real) <= 1.01 * (rh + rd) / lam_min
+
+
+def test_device_and_host_amg_give_the_same_port_impedance():
+    s = _two_bars()
+    h = handle_for(s)
+    dev = h.solve([1e9, 10e9], amg_on_device=1)
+    host = h.solve([1e9, 10e9], amg_on_device=0)
+    assert np.abs(dev["Z"] - host["Z"]).max() <= 1e-8 * np.abs(host["Z"]).max()
+    assert dev["stats"]["final_rre"] <= 1e-8 and host["stats"]["final_rre"] <= 1e-8
+    h.close()
