@@ -149,8 +149,10 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def pass_bytes(info, nb, csz):
-    """Algorithmic HBM bytes of each pass for one batched call (compulsory reads + writes)."""
+def pass_bytes(info, nb, csz, fused=False):
+    """Algorithmic HBM bytes of each pass for one batched call (compulsory reads + writes).
+    fused: the y/z/y passes run as one kernel (reported under z_pass) that reads and
+    writes only the active x-lines and reads the spectra."""
     K, M = info["K"], info["M"]
     nza, nrows = info["n_active_planes"], info["n_active_rows"]
     Kx, Px, Py = info["Kx"], info["Px"], info["Py"]
@@ -158,6 +160,16 @@ def pass_bytes(info, nb, csz):
     rows_line = 5 * nrows * Px * csz          # all active x-lines of one item, padded
     planes = 5 * nza * Py * Px * csz          # all active planes after the y transform
     vidx = 4 * nrows * Kx
+    if fused:
+        return {
+            "tucker_rebuild": 7 * Ht * 4,
+            "x_fwd": nb * (5 * K * csz + rows_line) + vidx,
+            "y_fwd": 0,
+            "z_pass": nb * 2 * rows_line + 7 * Ht * csz // 2 + 4 * nrows,
+            "y_inv": 0,
+            "x_inv_epilogue": nb * (rows_line + 5 * K * csz + 5 * K * csz + M * csz) + vidx + 40 * K,
+            "node_rows": nb * (5 * K * csz + M * csz) + 9 * M,
+        }
     return {
         "tucker_rebuild": 7 * Ht * 4,
         "x_fwd": nb * (5 * K * csz + rows_line) + vidx,
@@ -167,6 +179,22 @@ def pass_bytes(info, nb, csz):
         "x_inv_epilogue": nb * (rows_line + 5 * K * csz + 5 * K * csz + M * csz) + vidx + 40 * K,
         "node_rows": nb * (5 * K * csz + M * csz) + 9 * M,
     }
+
+
+# FP32 peak of the CUDA cores: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2.07 GHz (maximum SM clock)
+FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def fused_flops(info, nb):
+    """Algorithmic FP32 flops of the fused y/z/y kernel for one batched call: complex FFTs
+    counted as 5 N log2 N (the usual convention), the 5 x 5 block multiply as 17
+    complex-by-real multiply-adds (68 flops) per (ky, kz) point."""
+    import math
+    Px, Py, Pz, nza = info["Px"], info["Py"], info["Pz"], info["n_active_planes"]
+    fy = 5 * Py * math.log2(Py)
+    fz = 5 * Pz * math.log2(Pz)
+    per_kx = 2 * 5 * nza * fy + 5 * Py * 2 * fz + Py * Pz * 68
+    return nb * Px * per_kx
 
 
 def kernel_sources_sha():
@@ -413,7 +441,9 @@ def run_svh(args):
     value = ws * nb * Kt * args.steps / (ms / 1e3)
     # per-pass durations (CUDA events on the library's stream) over a second identical region
     _, (pass_ms, ncalls) = time_steps(h, torch, omega, x, y, args.steps, flush, profile=True)
-    pb = pass_bytes(info, nb, 8)
+    cnt, cho = h.pass_variants()
+    fused = bool(cnt[5] == 2 and cho[5] == 0)
+    pb = pass_bytes(info, nb, 8, fused)
     dom = max((k for k in pass_ms if k != "tucker_rebuild"), key=lambda k: pass_ms[k])
     per_launch_ms = pass_ms[dom] / ncalls
     peak, peak_kind = peaks()
@@ -421,11 +451,20 @@ def run_svh(args):
     traffic = traffic_from_profiles(dom, args.workload)
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
+                "path": "fused y/z/y" if fused else "separate passes",
                 "algorithmic_bytes_per_launch": pb[dom], "avg_launch_ms": per_launch_ms,
                 "share_of_step": pass_ms[dom] / sum(pass_ms.values()),
                 "pass_ms_per_step": {k: v / ncalls for k, v in pass_ms.items()},
                 "step_model_bytes": sum(pb.values()),
                 "step_model_frac": sum(pb.values()) / (ms / args.steps / 1e3) / 1e9 / peak}
+    if fused and dom == "z_pass":
+        # the fused kernel keeps its grids in shared memory: its bound is the FP32 ALUs
+        fl = fused_flops(info, nb)
+        tf = fl / (per_launch_ms / 1e3) / 1e12
+        roofline.update({"bound": "alu", "achieved": tf, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": tf / FP32_ALU_PEAK_TFLOPS, "peak_source": "derived: 152 SM x 128 FP32 x 2 x 2.07 GHz",
+                         "algorithmic_flops_per_launch": fl,
+                         "hbm_view": {"achieved_GBs": achieved, "frac": achieved / peak}})
     # FP64 product on the same workload
     fp64 = None
     if not args.no_fp64:

@@ -287,16 +287,19 @@ int svh_matvec_noalloc(svh_handle* h, double omega, int nb, const void* x_dev, v
  * The five FFT passes (0 x-forward with gather, 1 y-forward, 2 z pass,
  * 3 y-inverse, 4 x-inverse with epilogue) have size-specialised FP32 kernels
  * in several tile variants (radix split N1 x N2, threads per block, pruned
- * or full z pencils). svh_autotune times every variant of every pass on this
- * handle's grid for nb right-hand sides (zero data, 5 launches each, CUDA
- * events on the handle's stream) and keeps the fastest for later FP32
- * products; results are cached per process for equal grids and nb.
- * variants[5] and ms[5] (may be NULL) receive the choices and their
- * milliseconds per launch. svh_set_pass_variant forces one (SVH_ERR_ARG if
+ * or full z pencils). Choice 5 is the path: 0 fuses passes 1-3 into one
+ * kernel per (kx, item) that keeps the column's (basis, plane, y) slab in
+ * shared memory (when it fits and the active planes are contiguous), 1 runs
+ * the passes separately. svh_autotune times every variant of every pass on
+ * this handle's grid for nb right-hand sides (zero data, 5 launches each,
+ * CUDA events on the handle's stream), then the fused path against the
+ * separate passes, and keeps the fastest for later FP32 products; results
+ * are cached per process for equal grids and nb. variants[6] and ms[6] (may
+ * be NULL) receive the choices and their milliseconds per launch. svh_set_pass_variant forces one (SVH_ERR_ARG if
  * the pass has no such variant at this size); svh_get_pass_variants reports
  * the number of variants per pass (0: generic kernel) and the current choice.
  * FP64 products always use variant 0. */
-#define SVH_NFFTPASS 5
+#define SVH_NFFTPASS 6
 int svh_autotune(svh_handle* h, int nb, int32_t* variants, double* ms);
 int svh_set_pass_variant(svh_handle* h, int pass, int variant);
 int svh_get_pass_variants(const svh_handle* h, int32_t* counts, int32_t* chosen);

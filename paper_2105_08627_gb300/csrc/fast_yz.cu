@@ -85,15 +85,13 @@ bool run_yz_any(const PassArgs& a, size_t limit, cudaStream_t s, bool dry) {
 // The fused path (FP32): x forward onto B1T, one fused y/z/y kernel, x
 // inverse + epilogue from B1T. Needs contiguous active planes (shifted z
 // pencils), spectra resident in a.spec and the slab in shared memory.
-// dry_run: only report whether it applies.
-bool launch_fused_path(const PassArgs& a, size_t smem_limit, cudaStream_t s, bool dry_run) {
+bool fused_path_ok(const PassArgs& a, size_t smem_limit) {
     if (!a.zcontig || 2 * a.nza > a.Pz || !x_t_size(a.Px)) return false;
-    if (!run_yz_any(a, smem_limit, s, true)) return false;
-    if (dry_run) return true;
-    run_x_t(a, false, s);
-    run_yz_any(a, smem_limit, s, false);
-    run_x_t(a, true, s);
-    return true;
+    return run_yz_any(a, smem_limit, nullptr, true);
 }
+
+void launch_x_t(const PassArgs& a, bool inv, cudaStream_t s) { run_x_t(a, inv, s); }
+
+void launch_yz(const PassArgs& a, size_t smem_limit, cudaStream_t s) { run_yz_any(a, smem_limit, s, false); }
 
 }  // namespace svh

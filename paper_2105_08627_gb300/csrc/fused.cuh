@@ -380,6 +380,8 @@ __global__ void __launch_bounds__(NTX) k_xinv_t(const __grid_constant__ PassArgs
     }
 }
 
-bool launch_fused_path(const PassArgs& a, size_t smem_limit, cudaStream_t s, bool dry_run);
+bool fused_path_ok(const PassArgs& a, size_t smem_limit);
+void launch_x_t(const PassArgs& a, bool inv, cudaStream_t s);
+void launch_yz(const PassArgs& a, size_t smem_limit, cudaStream_t s);
 
 }  // namespace svh

@@ -26,6 +26,7 @@
 
 #include "fastpass.cuh"
 #include "fft.cuh"
+#include "fused.cuh"
 #include "svh_internal.h"
 
 namespace svh {
@@ -349,6 +350,14 @@ void matvec_scratch_bytes(const Handle* h, int nb, int precision, size_t* b1, si
     *b2 = (size_t)nb * 5 * nza * (size_t)h->Py * h->Px * csz;
 }
 
+static void ensure_smem_optin(Handle* h) {
+    if (h->smem_optin == 0) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+        h->smem_optin = (size_t)v;
+    }
+}
+
 // arguments of the size-specialised pass kernels for one product
 template <typename T>
 static PassArgs pass_args(Handle* h, double omega, const double* d_omegas, int nb, const void* x, void* y, int masked,
@@ -418,16 +427,19 @@ static int run_matvec(Handle* h, double omega, const double* d_omegas, int nb, c
     const uint8_t* d_rowmask = static_cast<const uint8_t*>(h->d_rowmask.p);
     PassArgs pa = pass_args<T>(h, omega, d_omegas, nb, x, y, masked, B1, B2);
     prof_mark(h, -1);
+    // the fused y/z/y path (FP32) when the slab fits shared memory and the tile choice allows it
+    ensure_smem_optin(h);
+    const bool fused = ti == 0 && h->tune32[5] == 0 && fused_path_ok(pa, h->smem_optin);
     // pass 3 needs the spectra: rebuild them from Tucker first when asked (Eq. 10)
     if (allow_rebuild && ti == 0 && h->kernel_mode == SVH_KERNELS_TUCKER_REBUILD) {
-        // every kernel has Tucker data in this mode; the size-specialised z
-        // pass takes the last mode product itself
-        bool fused = z_fast_size(Pz);
-        for (int u = 0; u < 7; ++u) fused = fused && h->tucker_on[u];
+        // every kernel has Tucker data in this mode; the separate size-specialised
+        // z pass takes the last mode product itself, the fused path reads them whole
+        bool fz = !fused && z_fast_size(Pz);
+        for (int u = 0; u < 7; ++u) fz = fz && h->tucker_on[u];
         TuckerFuse tf{};
-        int rc = launch_tucker_rebuild(h, fused ? &tf : nullptr);
+        int rc = launch_tucker_rebuild(h, fz ? &tf : nullptr);
         if (rc) return rc;
-        if (fused)
+        if (fz)
             for (int u = 0; u < 7; ++u) {
                 pa.tkW2[u] = tf.W2[u];
                 pa.tkF3[u] = tf.F3[u];
@@ -436,65 +448,76 @@ static int run_matvec(Handle* h, double omega, const double* d_omegas, int nb, c
     }
     prof_mark(h, 0);
     auto var = [&](int p) { return ti == 0 ? h->tune32[p] : 0; };
-    // pass 1
-    pa.var = var(0);
-    if (!launch_x_fast<T>(pa, false, h->stream)) {
-        int lpb = std::max(1, MAXPTS * NTHR / Px);
-        int64_t nlines = (int64_t)nb * 5 * nrows;
-        size_t sm = (size_t)(Px + lpb * (Px + 1)) * csz;
-        cudaFuncSetAttribute(k_xfwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        dim3 grid((unsigned)((nlines + lpb - 1) / lpb));
-        k_xfwd<T><<<grid, NTHR, sm, h->stream>>>(x, Nvec, K, vidx, rows, nrows, nza, h->Kx, h->Ky, B1,
-                                                 px, twx, lpb, nlines);
+    if (fused) {
+        launch_x_t(pa, false, h->stream);
+        prof_mark(h, 1);
+        prof_mark(h, 2);
+        launch_yz(pa, h->smem_optin, h->stream);
+        prof_mark(h, 3);
+        prof_mark(h, 4);
+        launch_x_t(pa, true, h->stream);
+        prof_mark(h, 5);
+    } else {
+        // pass 1
+        pa.var = var(0);
+        if (!launch_x_fast<T>(pa, false, h->stream)) {
+            int lpb = std::max(1, MAXPTS * NTHR / Px);
+            int64_t nlines = (int64_t)nb * 5 * nrows;
+            size_t sm = (size_t)(Px + lpb * (Px + 1)) * csz;
+            cudaFuncSetAttribute(k_xfwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            dim3 grid((unsigned)((nlines + lpb - 1) / lpb));
+            k_xfwd<T><<<grid, NTHR, sm, h->stream>>>(x, Nvec, K, vidx, rows, nrows, nza, h->Kx, h->Ky, B1,
+                                                     px, twx, lpb, nlines);
+        }
+        prof_mark(h, 1);
+        // pass 2
+        int tby = std::max(1, std::min(32, MAXPTS * NTHR / Py));
+        pa.var = var(1);
+        if (!launch_y_fast<T>(pa, false, h->stream)) {
+            size_t sm = (size_t)(Py + Py * tby) * csz;
+            cudaFuncSetAttribute(k_ycol<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            dim3 grid((Px + tby - 1) / tby, nza, nb * 5);
+            k_ycol<T, false><<<grid, NTHR, sm, h->stream>>>(B1, B2, nza, h->Ky, Py, Px, d_rowmask, py, twy, tby);
+        }
+        prof_mark(h, 2);
+        // pass 3
+        pa.var = var(2);
+        if (!launch_z_fast<T>(pa, h->stream)) {
+            int tbz = std::max(1, std::min(64, MAXPTS * NTHR / (5 * Pz)));
+            size_t sm = (size_t)(Pz + Pz * 5 * tbz) * csz;
+            cudaFuncSetAttribute(k_zpass<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            dim3 grid(nb, (Px + tbz - 1) / tbz, Py);
+            k_zpass<T><<<grid, NTHR, sm, h->stream>>>(B2, nb, nza, static_cast<const int32_t*>(h->d_zlist.p),
+                                                      Pz, Py, Px, h->Hx, h->Hy, h->Hz, spec, pz, twz, tbz);
+        }
+        prof_mark(h, 3);
+        // pass 4
+        pa.var = var(3);
+        if (!launch_y_fast<T>(pa, true, h->stream)) {
+            size_t sm = (size_t)(Py + Py * tby) * csz;
+            cudaFuncSetAttribute(k_ycol<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            dim3 grid((Px + tby - 1) / tby, nza, nb * 5);
+            k_ycol<T, true><<<grid, NTHR, sm, h->stream>>>(B2, B1, nza, h->Ky, Py, Px, d_rowmask, py, twy, tby);
+        }
+        prof_mark(h, 4);
+        // pass 5 + epilogue
+        pa.var = var(4);
+        if (!launch_x_fast<T>(pa, true, h->stream)) {
+            int lpb = std::max(1, MAXPTS * NTHR / Px);
+            int64_t nlines = (int64_t)nb * 5 * nrows;
+            size_t sm = (size_t)(Px + lpb * (Px + 1)) * csz;
+            cudaFuncSetAttribute(k_xinv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            const double mu = 4e-7 * 3.14159265358979323846;
+            T conv_scale = (T)(omega * mu * h->dx / ((double)Px * Py * Pz));
+            dim3 grid((unsigned)((nlines + lpb - 1) / lpb));
+            k_xinv<T><<<grid, NTHR, sm, h->stream>>>(
+                B1, x, y, Nvec, K, vidx, rows, nrows, nza, h->Kx, h->Ky,
+                static_cast<const int32_t*>(h->d_node.p), static_cast<const uint8_t*>(h->d_free.p),
+                static_cast<const double*>(h->d_lam.p), static_cast<const double*>(h->d_sig0.p), omega, mu,
+                h->dx, conv_scale, d_omegas, 1.0 / ((double)Px * Py * Pz), masked, px, twx, lpb, nlines);
+        }
+        prof_mark(h, 5);
     }
-    prof_mark(h, 1);
-    // pass 2
-    int tby = std::max(1, std::min(32, MAXPTS * NTHR / Py));
-    pa.var = var(1);
-    if (!launch_y_fast<T>(pa, false, h->stream)) {
-        size_t sm = (size_t)(Py + Py * tby) * csz;
-        cudaFuncSetAttribute(k_ycol<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        dim3 grid((Px + tby - 1) / tby, nza, nb * 5);
-        k_ycol<T, false><<<grid, NTHR, sm, h->stream>>>(B1, B2, nza, h->Ky, Py, Px, d_rowmask, py, twy, tby);
-    }
-    prof_mark(h, 2);
-    // pass 3
-    pa.var = var(2);
-    if (!launch_z_fast<T>(pa, h->stream)) {
-        int tbz = std::max(1, std::min(64, MAXPTS * NTHR / (5 * Pz)));
-        size_t sm = (size_t)(Pz + Pz * 5 * tbz) * csz;
-        cudaFuncSetAttribute(k_zpass<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        dim3 grid(nb, (Px + tbz - 1) / tbz, Py);
-        k_zpass<T><<<grid, NTHR, sm, h->stream>>>(B2, nb, nza, static_cast<const int32_t*>(h->d_zlist.p),
-                                                  Pz, Py, Px, h->Hx, h->Hy, h->Hz, spec, pz, twz, tbz);
-    }
-    prof_mark(h, 3);
-    // pass 4
-    pa.var = var(3);
-    if (!launch_y_fast<T>(pa, true, h->stream)) {
-        size_t sm = (size_t)(Py + Py * tby) * csz;
-        cudaFuncSetAttribute(k_ycol<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        dim3 grid((Px + tby - 1) / tby, nza, nb * 5);
-        k_ycol<T, true><<<grid, NTHR, sm, h->stream>>>(B2, B1, nza, h->Ky, Py, Px, d_rowmask, py, twy, tby);
-    }
-    prof_mark(h, 4);
-    // pass 5 + epilogue
-    pa.var = var(4);
-    if (!launch_x_fast<T>(pa, true, h->stream)) {
-        int lpb = std::max(1, MAXPTS * NTHR / Px);
-        int64_t nlines = (int64_t)nb * 5 * nrows;
-        size_t sm = (size_t)(Px + lpb * (Px + 1)) * csz;
-        cudaFuncSetAttribute(k_xinv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        const double mu = 4e-7 * 3.14159265358979323846;
-        T conv_scale = (T)(omega * mu * h->dx / ((double)Px * Py * Pz));
-        dim3 grid((unsigned)((nlines + lpb - 1) / lpb));
-        k_xinv<T><<<grid, NTHR, sm, h->stream>>>(
-            B1, x, y, Nvec, K, vidx, rows, nrows, nza, h->Kx, h->Ky,
-            static_cast<const int32_t*>(h->d_node.p), static_cast<const uint8_t*>(h->d_free.p),
-            static_cast<const double*>(h->d_lam.p), static_cast<const double*>(h->d_sig0.p), omega, mu,
-            h->dx, conv_scale, d_omegas, 1.0 / ((double)Px * Py * Pz), masked, px, twx, lpb, nlines);
-    }
-    prof_mark(h, 5);
     // node rows
     {
         int64_t n = M * nb;
@@ -530,8 +553,9 @@ int launch_matvec_on(Handle* h, double omega, int nb, const void* x, void* y, in
 }
 
 // ---- FFT tile autotuning
-static int pass_variants(const Handle* h, int p) {
+static int pass_variants(const Handle* h, int p, const PassArgs* pa = nullptr) {
     switch (p) {
+        case 5: return pa && fused_path_ok(*pa, h->smem_optin) ? 2 : 1;
         case 0: return x_fast_variants(h->Px, false, true);
         case 1: return y_fast_variants(h->Py, true);
         case 2: return z_fast_variants(h->Pz, true);
@@ -555,7 +579,7 @@ struct TuneKey {
     bool operator<(const TuneKey& o) const { return std::lexicographical_compare(v, v + 9, o.v, o.v + 9); }
 };
 static std::mutex g_tune_mu;
-static std::map<TuneKey, std::array<int, 5>> g_tune_cache;
+static std::map<TuneKey, std::array<int, 6>> g_tune_cache;
 
 int autotune(Handle* h, int nb, int32_t* variants, double* ms) {
     const TuneKey key{{h->Px, h->Py, h->Pz, (int)h->zlist.size(), (int)h->rows.size(), h->Kx, h->Ky, h->Kz, nb}};
@@ -563,7 +587,7 @@ int autotune(Handle* h, int nb, int32_t* variants, double* ms) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end() && !ms) {
-            for (int p = 0; p < 5; ++p) {
+            for (int p = 0; p < 6; ++p) {
                 h->tune32[p] = it->second[p];
                 if (variants) variants[p] = it->second[p];
             }
@@ -591,8 +615,9 @@ int autotune(Handle* h, int nb, int32_t* variants, double* ms) {
         cudaMemsetAsync(h->d_B2.p, 0, b2, s) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
         cudaEventCreate(&e1) != cudaSuccess)
         return done(set_err(h, SVH_ERR_CUDA, "svh_autotune: CUDA set-up failed"));
+    ensure_smem_optin(h);
     PassArgs pa = pass_args<float>(h, 2e9 * 3.14159265358979323846, nullptr, nb, x.p, y.p, 0, h->d_B1.p, h->d_B2.p);
-    std::array<int, 5> best{};
+    std::array<int, 6> best{};
     constexpr int REPS = 5;
     for (int p = 0; p < 5; ++p) {
         const int nv = pass_variants(h, p);
@@ -614,6 +639,38 @@ int autotune(Handle* h, int nb, int32_t* variants, double* ms) {
         if (variants) variants[p] = best[p];
         if (ms) ms[p] = tbest < 0 ? 0.0 : tbest / REPS;
     }
+    // 5: the fused y/z/y path against the separate passes with the variants just chosen
+    best[5] = 0;
+    if (pass_variants(h, 5, &pa) == 2) {
+        float t[2] = {0, 0};
+        for (int v = 0; v < 2; ++v) {
+            auto seq = [&]() {
+                if (v == 0) {
+                    launch_x_t(pa, false, s);
+                    launch_yz(pa, h->smem_optin, s);
+                    launch_x_t(pa, true, s);
+                } else {
+                    for (int p = 0; p < 5; ++p) {
+                        pa.var = best[p];
+                        launch_pass(pa, p, s);
+                    }
+                }
+            };
+            seq();
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < REPS; ++r) seq();
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+                return done(set_err(h, SVH_ERR_CUDA, "svh_autotune: launch failed"));
+            cudaEventElapsedTime(&t[v], e0, e1);
+        }
+        best[5] = t[1] < t[0] ? 1 : 0;
+        if (ms) ms[5] = t[best[5]] / REPS;
+    } else if (ms) {
+        ms[5] = 0.0;
+    }
+    h->tune32[5] = best[5];
+    if (variants) variants[5] = best[5];
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_tune_cache[key] = best;
@@ -622,15 +679,20 @@ int autotune(Handle* h, int nb, int32_t* variants, double* ms) {
 }
 
 int set_pass_variant(Handle* h, int pass, int variant) {
-    if (pass < 0 || pass >= 5 || variant < 0 || variant >= std::max(1, pass_variants(h, pass)))
+    ensure_smem_optin(h);
+    const PassArgs pa = pass_args<float>(h, 1.0, nullptr, 1, nullptr, nullptr, 0, nullptr, nullptr);
+    if (pass < 0 || pass >= 6 || variant < 0 || variant >= std::max(1, pass_variants(h, pass, &pa)))
         return set_err(h, SVH_ERR_ARG, "svh_set_pass_variant: no such pass or variant at this size");
     h->tune32[pass] = variant;
     return SVH_OK;
 }
 
-void get_pass_variants(const Handle* h, int32_t* counts, int32_t* chosen) {
-    for (int p = 0; p < 5; ++p) {
-        if (counts) counts[p] = pass_variants(h, p);
+void get_pass_variants(const Handle* hc, int32_t* counts, int32_t* chosen) {
+    Handle* h = const_cast<Handle*>(hc);   // reads the grid only (and caches a device attribute)
+    ensure_smem_optin(h);
+    const PassArgs pa = pass_args<float>(h, 1.0, nullptr, 1, nullptr, nullptr, 0, nullptr, nullptr);
+    for (int p = 0; p < 6; ++p) {
+        if (counts) counts[p] = pass_variants(h, p, &pa);
         if (chosen) chosen[p] = h->tune32[p];
     }
 }

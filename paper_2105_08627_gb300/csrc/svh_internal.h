@@ -90,7 +90,8 @@ struct Handle {
     DevBuf d_B1, d_B2;
     DevBuf d_xin, d_yout;              // staging for svh_matvec_host
     DevBuf d_omegas;                   // per-item frequencies for svh_matvec_omegas
-    int tune32[5] = {0, 0, 0, 0, 0};   // FP32 tile variant per FFT pass (svh_autotune)
+    int tune32[6] = {0, 0, 0, 0, 0, 0};   // FP32 tile variant per FFT pass, [5]: 0 fused y/z/y, 1 separate
+    size_t smem_optin = 0;                // opt-in shared memory per block of the device
 };
 
 int set_err(Handle* h, int code, const std::string& msg);

@@ -429,13 +429,14 @@ class Handle:
 
     PASSES = ("tucker_rebuild", "x_fwd", "y_fwd", "z_pass", "y_inv", "x_inv_epilogue", "node_rows")
 
-    FFT_PASSES = ("x_fwd", "y_fwd", "z_pass", "y_inv", "x_inv_epilogue")
+    FFT_PASSES = ("x_fwd", "y_fwd", "z_pass", "y_inv", "x_inv_epilogue", "path")
 
     def autotune(self, nb):
-        """Time every FP32 tile variant of the five FFT passes for nb items and keep
-        the fastest -> (variants[5], ms per launch[5])."""
-        v = np.zeros(5, np.int32)
-        ms = np.zeros(5)
+        """Time every FP32 tile variant of the five FFT passes for nb items, then the
+        fused y/z/y path against the separate passes, and keep the fastest
+        -> (variants[6], ms per launch[6]); variants[5]: 0 fused, 1 separate."""
+        v = np.zeros(6, np.int32)
+        ms = np.zeros(6)
         self._ck(lib().svh_autotune(self._h, int(nb), _i32p(v), _dp(ms)), "svh_autotune")
         return v, ms
 
@@ -443,9 +444,10 @@ class Handle:
         self._ck(lib().svh_set_pass_variant(self._h, int(p), int(v)), "svh_set_pass_variant")
 
     def pass_variants(self):
-        """-> (number of variants per FFT pass (0: generic kernel), current choice)."""
-        n = np.zeros(5, np.int32)
-        c = np.zeros(5, np.int32)
+        """-> (number of variants per FFT pass (0: generic kernel), current choice);
+        entry 5 is the path (2 choices when the fused y/z/y kernel applies)."""
+        n = np.zeros(6, np.int32)
+        c = np.zeros(6, np.int32)
         self._ck(lib().svh_get_pass_variants(self._h, _i32p(n), _i32p(c)), "svh_get_pass_variants")
         return n, c
 

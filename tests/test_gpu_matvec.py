@@ -221,6 +221,10 @@ def test_meander_256x256x8_full_size():
         assert rel_err(y64[b], yref[b]) <= FP64_TOL
     y32 = h.matvec(om, torch.from_numpy(x.astype(np.complex64)).cuda()).cpu().numpy().astype(np.complex128)
     _check_fp32(y32, yref)
+    assert h.pass_variants()[0][5] == 2          # the fused y/z/y path applies (and ran above)
+    h.set_pass_variant(5, 1)                     # separate y, z, y passes
+    y32s = h.matvec(om, torch.from_numpy(x.astype(np.complex64)).cuda()).cpu().numpy().astype(np.complex128)
+    _check_fp32(y32s, yref)
     h.close()
 
 
@@ -253,12 +257,14 @@ def test_esfq_512x512x24_sampled_rows():
     h.close()
 
 
-@pytest.mark.parametrize("seed,shape", [
-    (61, (64, 16, 8)),     # P = 128, 32, 16: transposed-split variants on x and y
-    (62, (48, 24, 12)),    # P = 96, 48, 24: x inverse without a grouped kernel
+@pytest.mark.parametrize("seed,shape,fused", [
+    (61, (64, 16, 8), False),     # P = 128, 32, 16: transposed-split variants on x and y
+    (62, (48, 24, 12), False),    # P = 96, 48, 24: x inverse without a grouped kernel
+    (63, (64, 64, 8), True),      # P = 128, 128, 16: the fused y/z/y path applies
+    (64, (128, 128, 4), True),    # P = 256, 256, 8
 ])
-def test_every_tile_variant_and_autotune(seed, shape):
-    """a12: each FFT tile variant the autotuner may pick gives the oracle's product."""
+def test_every_tile_variant_and_autotune(seed, shape, fused):
+    """a12: each FFT tile variant and path the autotuner may pick gives the oracle's product."""
     torch = _torch()
     s = S.random_blob(seed, *shape, fill=0.5)
     g, S7, Pr, T = oracle_reference(s)
@@ -269,17 +275,28 @@ def test_every_tile_variant_and_autotune(seed, shape):
     h = handle_for(s, toeplitz=T)
     xd = torch.from_numpy(x.astype(np.complex64)).cuda()
     counts, chosen = h.pass_variants()
-    assert np.all(counts >= 2) and np.all(chosen == 0)
+    assert np.all(counts[:5] >= 2) and np.all(chosen == 0)
+    assert counts[5] == (2 if fused else 1)
+    _check_fp32(h.matvec(om, xd).cpu().numpy().astype(np.complex128), yref)   # default path
+    if fused:
+        h.set_pass_variant(5, 1)                                                # separate passes
     for p in range(5):
         for v in range(counts[p]):
             h.set_pass_variant(p, v)
             y = h.matvec(om, xd).cpu().numpy().astype(np.complex128)
             _check_fp32(y, yref)
         h.set_pass_variant(p, 0)
+    h.set_pass_variant(5, 0)
     with pytest.raises(Exception):
         h.set_pass_variant(0, counts[0])
+    with pytest.raises(Exception):
+        h.set_pass_variant(5, counts[5])
     v, ms = h.autotune(nb)
-    assert np.all((v >= 0) & (v < counts)) and np.all(ms > 0)
+    assert np.all((v >= 0) & (v < np.maximum(counts, 1))) and np.all(ms[:5] > 0)
     assert np.array_equal(h.pass_variants()[1], v)
     _check_fp32(h.matvec(om, xd).cpu().numpy().astype(np.complex128), yref)
+    # FP64 products ignore the FP32 tile choices and the fused path
+    y64 = h.matvec(om, torch.from_numpy(x).cuda()).cpu().numpy()
+    for b in range(nb):
+        assert rel_err(y64[b], yref[b]) <= FP64_TOL
     h.close()
