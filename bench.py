@@ -442,7 +442,7 @@ def run_svh(args):
     # per-pass durations (CUDA events on the library's stream) over a second identical region
     _, (pass_ms, ncalls) = time_steps(h, torch, omega, x, y, args.steps, flush, profile=True)
     cnt, cho = h.pass_variants()
-    fused = bool(cnt[5] == 2 and cho[5] == 0)
+    fused = bool(cnt[5] == 2 and cho[5] == 1)
     pb = pass_bytes(info, nb, 8, fused)
     dom = max((k for k in pass_ms if k != "tucker_rebuild"), key=lambda k: pass_ms[k])
     per_launch_ms = pass_ms[dom] / ncalls

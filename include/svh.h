@@ -287,10 +287,10 @@ int svh_matvec_noalloc(svh_handle* h, double omega, int nb, const void* x_dev, v
  * The five FFT passes (0 x-forward with gather, 1 y-forward, 2 z pass,
  * 3 y-inverse, 4 x-inverse with epilogue) have size-specialised FP32 kernels
  * in several tile variants (radix split N1 x N2, threads per block, pruned
- * or full z pencils). Choice 5 is the path: 0 fuses passes 1-3 into one
- * kernel per (kx, item) that keeps the column's (basis, plane, y) slab in
- * shared memory (when it fits and the active planes are contiguous), 1 runs
- * the passes separately. svh_autotune times every variant of every pass on
+ * or full z pencils). Choice 5 is the path: 0 runs the passes separately,
+ * 1 fuses passes 1-3 into one kernel per (kx, item) that keeps the column's
+ * (basis, plane, y) slab in shared memory (offered when it fits and the
+ * active planes are contiguous). svh_autotune times every variant of every pass on
  * this handle's grid for nb right-hand sides (zero data, 5 launches each,
  * CUDA events on the handle's stream), then the fused path against the
  * separate passes, and keeps the fastest for later FP32 products; results
@@ -300,6 +300,11 @@ int svh_matvec_noalloc(svh_handle* h, double omega, int nb, const void* x_dev, v
  * the number of variants per pass (0: generic kernel) and the current choice.
  * FP64 products always use variant 0. */
 #define SVH_NFFTPASS 6
+/* Device status word of the handle: bit 0 (SVH_STATUS_TMA_TIMEOUT) is set
+ * when a kernel's bounded wait for a TMA copy expired (its results are then
+ * invalid). clear != 0 resets it. */
+#define SVH_STATUS_TMA_TIMEOUT 1
+int svh_get_device_status(svh_handle* h, int32_t* status, int clear);
 int svh_autotune(svh_handle* h, int nb, int32_t* variants, double* ms);
 int svh_set_pass_variant(svh_handle* h, int pass, int variant);
 int svh_get_pass_variants(const svh_handle* h, int32_t* counts, int32_t* chosen);
@@ -341,6 +346,24 @@ int svh_host_amg_solve(int n, const int32_t* rowptr, const int32_t* colidx, cons
  * Errors as svh_host_amg_solve, plus SVH_ERR_CUDA. */
 int svh_device_amg_solve(int n, const int32_t* rowptr, const int32_t* colidx, const double* vals, const double* b,
                          double* x, int nrhs, double tol, int maxit, int32_t* iters, int32_t* levels);
+/* ---- Algorithm 2: install-time store of the unit Toeplitz tensors.
+ * svh_toeplitz_store_write compresses the 7 unit Toeplitz tensors of a
+ * Kx x Ky x Kz domain, T[7][Kz][Ky][Kx] (the layout of svh_load_toeplitz),
+ * with Algorithm 1 at tol and writes their Tucker cores and factors to path;
+ * T = NULL computes them on the current CUDA device first (the quadrature of
+ * svh_generate_toeplitz). svh_toeplitz_store_read restores (Eq. 10) the
+ * leading Kx x Ky x Kz block of each tensor into T (host, 7*Kx*Ky*Kz
+ * doubles); ranks[21] (may be NULL) receives the stored ranks. The unit
+ * kernels are dimensionless (the voxel size enters the product as
+ * j omega mu dx), so a store serves every voxel size and the crop needs no
+ * scaling. svh_load_toeplitz_store reads the handle's grid size from a store
+ * and installs the result as svh_load_toeplitz does. All return SVH_ERR_ARG
+ * for an unreadable or foreign file or a grid larger than the stored one.
+ * The file is in host byte order. */
+int svh_toeplitz_store_write(const char* path, int Kx, int Ky, int Kz, const double* T, double tol);
+int svh_toeplitz_store_read(const char* path, int Kx, int Ky, int Kz, double* T, int32_t* ranks);
+int svh_load_toeplitz_store(svh_handle* h, const char* path);
+
 /* Algorithm 1 (Tucker-SVD) of a real D1 x D2 x D3 array O stored with the
  * mode-1 index fastest, O[(i3*D2 + i2)*D1 + i1]. The rank of mode i is the
  * smallest d_i whose discarded singular values have 2-norm <= tol/sqrt(3) *

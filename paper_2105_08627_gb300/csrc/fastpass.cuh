@@ -11,12 +11,14 @@
 // every HBM access is a coalesced row segment and each point crosses shared
 // memory once. The z pass keeps one whole Pz-point line per thread.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include <type_traits>
 
 #include "fft_reg.cuh"
+#include "svh.h"
 
 namespace svh {
 
@@ -46,14 +48,10 @@ struct PassArgs {
     double inv_P;            // 1 / (Px Py Pz)
     int masked;
     int zcontig;             // 1 when the active planes are consecutive
-    // Tucker rebuild fused into the z pass (FP32 only): kernel u's spectra
-    // S_u[kz][ky][kx] = sum_c F3_u[kz][c] W2_u[c][ky][kx] (Eq. 10, mode 3) are
-    // formed while the pass loads them; tkW2[u] == nullptr: read spec
-    const float* tkW2[7];
-    const float* tkF3[7];
-    int tkd3[7];
     int var;                 // tile variant of the pass being launched (0: default)
+    int* status;             // device status word: kernels set bits on a bounded wait that timed out
 };
+
 
 // outward flux of basis alpha through face f (-x,+x,-y,+y,-z,+z)
 __device__ __forceinline__ float face_flux(int a, int f) {
@@ -445,9 +443,7 @@ __device__ __forceinline__ void block_multiply5(typename CT<T>::type* io, T g, T
 // shared memory sp[u][kz][lane], with the odd S-kernel signs folded in: only
 // the octant |k| <= P/2 is stored, so kz and PZ - kz share the value at
 // az = min(kz, PZ - kz) (Sz flips sign in the upper half, Sx/Sy by column/row).
-// One task per (kernel, column): in the fused Tucker mode its d3 mode-2 values
-// are read once and contracted with F3 for every az (same fmaf order as the
-// separate mode-3 restore, so both give identical spectra).
+// One task per (kernel, column), each octant value loaded once.
 template <typename T, int PZ>
 __device__ __forceinline__ void load_tile_spectra(const PassArgs& a, T (*sp)[PZ][32], int kx0, int ky) {
     constexpr int NH = PZ / 2 + 1;
@@ -464,25 +460,8 @@ __device__ __forceinline__ void load_tile_spectra(const PassArgs& a, T (*sp)[PZ]
         const T sg = u == 1 ? sgx : (u == 2 ? sgy : (T)1);
         const int64_t off = (int64_t)ay * a.Hx + ax;
         T val[NH];
-        const float* W2 = std::is_same<T, float>::value ? a.tkW2[u] : nullptr;
-        if (W2) {
-            const int d3 = a.tkd3[u];
-            const float* F3 = a.tkF3[u];
-            float w[NH];
 #pragma unroll
-            for (int c = 0; c < NH; ++c) w[c] = c < d3 ? __ldg(W2 + c * plane + off) : 0.f;
-#pragma unroll
-            for (int az = 0; az < NH; ++az) {
-                float acc = 0.f;
-#pragma unroll
-                for (int c = 0; c < NH; ++c)
-                    if (c < d3) acc = fmaf(__ldg(F3 + az * d3 + c), w[c], acc);
-                val[az] = (T)acc;
-            }
-        } else {
-#pragma unroll
-            for (int az = 0; az < NH; ++az) val[az] = __ldg(spec + u * Sk + az * plane + off);
-        }
+        for (int az = 0; az < NH; ++az) val[az] = __ldg(spec + u * Sk + az * plane + off);
 #pragma unroll
         for (int az = 0; az < NH; ++az) {
             sp[u][az][ln] = sg * val[az];
@@ -634,6 +613,146 @@ __global__ void __launch_bounds__(160) k_zpass_half(const __grid_constant__ Pass
                 if (zi < nza) B2[base + zi * plane] = w[zi];
         }
     }
+}
+
+// ---------------------------------------------------------------- TMA-staged z pass
+// Same arithmetic as k_zpass_half; the 5 nza active planes of a (32-kx, ky)
+// tile of one item travel as one TMA box (cp.async.bulk.tensor, 3-D view of
+// B2 as [planes][Py][2 Px] floats) into shared memory, double-buffered so the
+// next item's box arrives while this one is transformed, and the results go
+// back by a TMA store from the same buffer. One thread issues the copies;
+// every wait is bounded (SVH_STATUS_TMA_TIMEOUT in a.status on expiry).
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const void* tmap, uint64_t* bar, int c0, int c1, int c2) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(smem_u32(dst)),
+        "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tma_store_3d(const void* tmap, const void* src, int c0, int c1, int c2) {
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(tmap),
+                 "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(src))
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// tmap: 3-D float view of B2, dims {2 Px, Py, nb 5 nza}, box {64, 1, 5 nza}
+template <int PZ>
+__global__ void __launch_bounds__(160) k_zpass_tma(const __grid_constant__ PassArgs a, const __grid_constant__ CUtensorMap tmap) {
+    using C = float2;
+    constexpr int NH = PZ / 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    // TMA boxes start on a 128-byte boundary (the launch adds 128 bytes of slack)
+    unsigned char* base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+    const int nza = a.nza, nq = 5 * nza;
+    C* tile = reinterpret_cast<C*>(base);                                      // [2][nq][32]
+    C(*buf)[PZ][32] = reinterpret_cast<C(*)[PZ][32]>(tile + 2 * nq * 32);      // [5][PZ][32]
+    float(*sp)[PZ][32] = reinterpret_cast<float(*)[PZ][32]>(buf + 5);          // [7][PZ][32]
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sp + 7);                       // [2]
+    const int al = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int kx0 = blockIdx.x * 32;
+    const int ky = blockIdx.y;
+    const uint32_t box_bytes = (uint32_t)nq * 32 * sizeof(C);
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_async_smem();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_expect_tx(&bar[0], box_bytes);
+        tma_load_3d(tile, &tmap, &bar[0], 2 * kx0, ky, 0);
+    }
+    load_tile_spectra<float, PZ>(a, sp, kx0, ky);
+    bool failed = false;
+    for (int b = 0; b < a.nb; ++b) {
+        const int cur = b & 1;
+        C* tb = tile + cur * nq * 32;
+        if (threadIdx.x == 0 && b + 1 < a.nb) {
+            bulk_wait_read0();   // item b - 1's store has read the other buffer
+            mbar_expect_tx(&bar[cur ^ 1], box_bytes);
+            tma_load_3d(tile + (cur ^ 1) * nq * 32, &tmap, &bar[cur ^ 1], 2 * kx0, ky, (b + 1) * nq);
+        }
+        // bounded wait for this item's box
+        {
+            const uint32_t parity = (uint32_t)(b >> 1) & 1u;
+            int spins = 0;
+            while (!mbar_try_wait(&bar[cur], parity)) {
+                if (++spins > (1 << 20)) { failed = true; break; }
+            }
+        }
+        if (__syncthreads_or(failed)) {
+            if (threadIdx.x == 0) {
+                atomicOr(a.status, SVH_STATUS_TMA_TIMEOUT);
+                // drain (bounded) the load issued for the next item before the CTA exits
+                if (b + 1 < a.nb) {
+                    int spins = 0;
+                    while (!mbar_try_wait(&bar[cur ^ 1], (uint32_t)((b + 1) >> 1) & 1u) && ++spins < (1 << 20)) {
+                    }
+                }
+            }
+            break;
+        }
+        C pre[NH];
+#pragma unroll
+        for (int zi = 0; zi < NH; ++zi) pre[zi] = zi < nza ? tb[(al * nza + zi) * 32 + lane] : make_float2(0.f, 0.f);
+        {
+            C v[PZ];
+            reg_fft_lowin<PZ, false>(pre, v);
+#pragma unroll
+            for (int z = 0; z < PZ; ++z) buf[al][z][lane] = v[z];
+        }
+        __syncthreads();
+        for (int task = threadIdx.x; task < PZ * 32; task += 160) {
+            const int kz = task >> 5, ln = task & 31;
+            C io[5];
+#pragma unroll
+            for (int q = 0; q < 5; ++q) io[q] = buf[q][kz][ln];
+            block_multiply5<float>(io, sp[0][kz][ln], sp[1][kz][ln], sp[2][kz][ln], sp[3][kz][ln], sp[4][kz][ln],
+                                   sp[5][kz][ln], sp[6][kz][ln]);
+#pragma unroll
+            for (int q = 0; q < 5; ++q) buf[q][kz][ln] = io[q];
+        }
+        __syncthreads();
+        {
+            C v[PZ], w[NH];
+#pragma unroll
+            for (int z = 0; z < PZ; ++z) v[z] = buf[al][z][lane];
+            reg_fft_lowout<PZ, true>(v, w);
+#pragma unroll
+            for (int zi = 0; zi < NH; ++zi)
+                if (zi < nza) tb[(al * nza + zi) * 32 + lane] = w[zi];
+        }
+        fence_async_smem();   // this thread's writes to the box, visible to the TMA store
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            tma_store_3d(&tmap, tb, 2 * kx0, ky, b * nq);
+            bulk_commit();
+        }
+    }
+    if (threadIdx.x == 0) bulk_wait0();   // the stores have finished before shared memory is released
 }
 
 // launchers (return false when the size has no specialised kernel)

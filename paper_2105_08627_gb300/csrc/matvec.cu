@@ -395,6 +395,7 @@ static PassArgs pass_args(Handle* h, double omega, const double* d_omegas, int n
     pa.zcontig = 1;
     for (int i = 1; i < nza; ++i)
         if (h->zlist[i] != h->zlist[0] + i) pa.zcontig = 0;
+    pa.status = static_cast<int*>(h->d_status.p);
     return pa;
 }
 
@@ -429,22 +430,11 @@ static int run_matvec(Handle* h, double omega, const double* d_omegas, int nb, c
     prof_mark(h, -1);
     // the fused y/z/y path (FP32) when the slab fits shared memory and the tile choice allows it
     ensure_smem_optin(h);
-    const bool fused = ti == 0 && h->tune32[5] == 0 && fused_path_ok(pa, h->smem_optin);
+    const bool fused = ti == 0 && h->tune32[5] == 1 && fused_path_ok(pa, h->smem_optin);
     // pass 3 needs the spectra: rebuild them from Tucker first when asked (Eq. 10)
     if (allow_rebuild && ti == 0 && h->kernel_mode == SVH_KERNELS_TUCKER_REBUILD) {
-        // every kernel has Tucker data in this mode; the separate size-specialised
-        // z pass takes the last mode product itself, the fused path reads them whole
-        bool fz = !fused && z_fast_size(Pz);
-        for (int u = 0; u < 7; ++u) fz = fz && h->tucker_on[u];
-        TuckerFuse tf{};
-        int rc = launch_tucker_rebuild(h, fz ? &tf : nullptr);
+        int rc = launch_tucker_rebuild(h);
         if (rc) return rc;
-        if (fz)
-            for (int u = 0; u < 7; ++u) {
-                pa.tkW2[u] = tf.W2[u];
-                pa.tkF3[u] = tf.F3[u];
-                pa.tkd3[u] = tf.d3[u];
-            }
     }
     prof_mark(h, 0);
     auto var = [&](int p) { return ti == 0 ? h->tune32[p] : 0; };
@@ -639,13 +629,13 @@ int autotune(Handle* h, int nb, int32_t* variants, double* ms) {
         if (variants) variants[p] = best[p];
         if (ms) ms[p] = tbest < 0 ? 0.0 : tbest / REPS;
     }
-    // 5: the fused y/z/y path against the separate passes with the variants just chosen
+    // 5: the separate passes (with the variants just chosen) against the fused y/z/y path
     best[5] = 0;
     if (pass_variants(h, 5, &pa) == 2) {
         float t[2] = {0, 0};
         for (int v = 0; v < 2; ++v) {
             auto seq = [&]() {
-                if (v == 0) {
+                if (v == 1) {
                     launch_x_t(pa, false, s);
                     launch_yz(pa, h->smem_optin, s);
                     launch_x_t(pa, true, s);

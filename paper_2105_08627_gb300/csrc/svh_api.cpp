@@ -116,7 +116,8 @@ static void free_all(Handle* h) {
     prof_release(h);
     precond_free(h);
     for (DevBuf* b : {&h->d_vidx, &h->d_rows, &h->d_rowmask, &h->d_zlist, &h->d_node, &h->d_ninc,
-                      &h->d_free, &h->d_lam, &h->d_sig0, &h->d_B1, &h->d_B2, &h->d_xin, &h->d_yout, &h->d_omegas})
+                      &h->d_free, &h->d_lam, &h->d_sig0, &h->d_B1, &h->d_B2, &h->d_xin, &h->d_yout, &h->d_omegas,
+                      &h->d_status})
         dev_free(*b);
 }
 
@@ -631,6 +632,10 @@ int svh_setup_grid(svh_handle* hh, int Kx, int Ky, int Kz, double dx, const uint
     if ((rc = dev_upload(h, h->d_free, freem.data(), freem.size()))) return rc;
     if ((rc = dev_upload(h, h->d_lam, h->lam.data(), K * 8))) return rc;
     if ((rc = dev_upload(h, h->d_sig0, h->sig0.data(), K * 8))) return rc;
+    if (!h->d_status.p) {
+        const int32_t zero = 0;
+        if ((rc = dev_upload(h, h->d_status, &zero, 4))) return rc;
+    }
     h->have_grid = true;
     return SVH_OK;
 }
@@ -793,6 +798,18 @@ int svh_matvec(svh_handle* hh, double omega, int nb, const void* x, void* y, int
     const char* yc = static_cast<const char*>(y);
     if (xc < yc + bytes && yc < xc + bytes) return set_err(h, SVH_ERR_ARG, "svh_matvec: x and y overlap");
     return precision == SVH_FP32 ? launch_matvec32(h, omega, nb, x, y, 0) : launch_matvec64(h, omega, nb, x, y, 0);
+}
+
+int svh_get_device_status(svh_handle* hh, int32_t* status, int clear) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    HCHECK(h);
+    if (!status) return SVH_ERR_ARG;
+    *status = 0;
+    if (!h->d_status.p) return SVH_OK;
+    SVH_CUDA_TRY(h, cudaMemcpyAsync(status, h->d_status.p, 4, cudaMemcpyDeviceToHost, h->stream));
+    if (clear) SVH_CUDA_TRY(h, cudaMemsetAsync(h->d_status.p, 0, 4, h->stream));
+    SVH_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    return SVH_OK;
 }
 
 int svh_autotune(svh_handle* hh, int nb, int32_t* variants, double* ms) {

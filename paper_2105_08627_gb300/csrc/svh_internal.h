@@ -90,7 +90,8 @@ struct Handle {
     DevBuf d_B1, d_B2;
     DevBuf d_xin, d_yout;              // staging for svh_matvec_host
     DevBuf d_omegas;                   // per-item frequencies for svh_matvec_omegas
-    int tune32[6] = {0, 0, 0, 0, 0, 0};   // FP32 tile variant per FFT pass, [5]: 0 fused y/z/y, 1 separate
+    DevBuf d_status;                   // int32 status word set by kernels (bounded waits that expired)
+    int tune32[6] = {0, 0, 0, 0, 0, 0};   // FP32 tile variant per FFT pass, [5]: 0 separate passes, 1 fused y/z/y
     size_t smem_optin = 0;                // opt-in shared memory per block of the device
 };
 
@@ -149,15 +150,8 @@ void amg_dev_destroy(void* d);
 // b = S^{-1} e on the device; e, b: double2 [nb][nf] device arrays
 int precond_schur_solve_dev(Handle* h, int nb, int per_freq, const void* e_dev, void* b_dev);
 // Tucker rebuild (tucker.cu)
-// restore the FP32 spectra from Tucker data (Eq. 10); with fuse != nullptr
-// the last mode product is left to the z pass: fuse receives, per kernel, the
-// mode-2 result W2[c][Hy][Hx], the factor F3[Hz][d3] and d3
-struct TuckerFuse {
-    const float* W2[7];
-    const float* F3[7];
-    int d3[7];
-};
-int launch_tucker_rebuild(Handle* h, TuckerFuse* fuse = nullptr);
+// restore the FP32 spectra from Tucker data (Eq. 10) into d_spec32
+int launch_tucker_rebuild(Handle* h);
 
 }  // namespace svh
 

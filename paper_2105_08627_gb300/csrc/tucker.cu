@@ -7,7 +7,8 @@
 //   W2[c][ky][kx] = sum_b W1[c][b][kx] F2[ky][b]
 //   S[kz][ky][kx] = sum_c W2[c][ky][kx] F3[kz][c]
 // Modes 1 and 2 are batches of GEMMs on the tensor cores (3xTF32, one launch
-// per stage for all kernels); mode 3 (d3, Hz ~ Pz/2) is a streaming kernel.
+// per stage for all kernels); mode 3 (d3, Hz ~ Pz/2) is a streaming kernel
+// (k_mode3_h, its plane count a compile-time constant).
 // The S and Q spectra keep ranks of 100-250 per mode at tol = 1e-8 (only G00
 // compresses to ~20), so the restore is a real dense contraction of about
 // 2.5 GFLOP at 512 x 512 x 16. The three-way TF32 split keeps the rebuilt
@@ -178,7 +179,7 @@ __global__ void __launch_bounds__(256) k_mode3(const __grid_constant__ Mode3 a) 
 
 // k_mode3 with the plane count a compile-time constant (Hz = Pz / 2 + 1 of
 // the specialised z sizes): d3 <= Hz values per point in registers, no
-// shared memory, the same fmaf order as k_mode3 and the fused z pass.
+// shared memory, the same fmaf order as k_mode3.
 template <int NH>
 __global__ void __launch_bounds__(256) k_mode3_h(const __grid_constant__ Mode3 a) {
     const int s = blockIdx.y;
@@ -212,7 +213,7 @@ static bool launch_mode3_h(const Mode3& m3, int nz, cudaStream_t st) {
     }
 }
 
-int launch_tucker_rebuild(Handle* h, TuckerFuse* fuse) {
+int launch_tucker_rebuild(Handle* h) {
     const int Hx = h->Hx, Hy = h->Hy, Hz = h->Hz;
     const int64_t Ht = (int64_t)Hx * Hy * Hz;
     size_t n1 = 0, n2 = 0;
@@ -279,15 +280,6 @@ int launch_tucker_rebuild(Handle* h, TuckerFuse* fuse) {
     }
     // mode 3
     const int nz = h->tk_probs_split[2];
-    if (fuse) {
-        for (int i = 0; i < nz && i < 7; ++i) {
-            fuse->W2[i] = all[off + i].B;
-            fuse->F3[i] = all[off + i].A;
-            fuse->d3[i] = all[off + i].K;
-        }
-        SVH_CUDA_TRY(h, cudaGetLastError());
-        return SVH_OK;
-    }
     bool small = Hz <= 64;
     for (int i = 0; i < nz; ++i) small = small && all[off + i].K <= 64;
     if (small && nz) {

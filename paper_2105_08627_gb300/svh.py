@@ -113,6 +113,7 @@ SIGNATURES = {
                                   C.POINTER(svh_stats)]),
     "svh_profile_begin": (C.c_int, [_P, C.c_int]),
     "svh_autotune": (C.c_int, [_P, C.c_int, _I32P, _DP]),
+    "svh_get_device_status": (C.c_int, [_P, _I32P, C.c_int]),
     "svh_set_pass_variant": (C.c_int, [_P, C.c_int, C.c_int]),
     "svh_get_pass_variants": (C.c_int, [_P, _I32P, _I32P]),
     "svh_profile_end": (C.c_int, [_P, _DP, _I32P]),
@@ -121,6 +122,9 @@ SIGNATURES = {
     "svh_host_amg_solve": (C.c_int, [C.c_int, _I32P, _I32P, _DP, _DP, _DP, C.c_double, C.c_int, _I32P, _I32P]),
     "svh_device_amg_solve": (C.c_int, [C.c_int, _I32P, _I32P, _DP, _DP, _DP, C.c_int, C.c_double, C.c_int, _I32P,
                                         _I32P]),
+    "svh_toeplitz_store_write": (C.c_int, [C.c_char_p, C.c_int, C.c_int, C.c_int, _DP, C.c_double]),
+    "svh_toeplitz_store_read": (C.c_int, [C.c_char_p, C.c_int, C.c_int, C.c_int, _DP, _I32P]),
+    "svh_load_toeplitz_store": (C.c_int, [_P, C.c_char_p]),
     "svh_host_tucker_svd": (C.c_int, [_DP, C.c_int, C.c_int, C.c_int, C.c_double, _I32P, _DP, _DP, _DP, _DP]),
 }
 
@@ -213,6 +217,29 @@ def device_amg_solve(S, b, tol=1e-8, maxit=500):
     return x.reshape(shape), it.value, lv.value
 
 
+def toeplitz_store_write(path, K, tol, T=None):
+    """Algorithm 2, install stage: store the Tucker data of the unit Toeplitz tensors of a
+    K = (Kx, Ky, Kz) domain (T[7, Kz, Ky, Kx] given, or None: computed on the current device)."""
+    Kx, Ky, Kz = (int(v) for v in K)
+    Tp = None
+    if T is not None:
+        T = np.ascontiguousarray(T, np.float64)
+        if T.shape != (7, Kz, Ky, Kx):
+            raise ValueError("T must have shape (7, Kz, Ky, Kx)")
+        Tp = _dp(T)
+    _check_host(lib().svh_toeplitz_store_write(os.fsencode(path), Kx, Ky, Kz, Tp, tol), "svh_toeplitz_store_write")
+
+
+def toeplitz_store_read(path, K):
+    """Algorithm 2, set-up stage: the leading K block of the stored tensors -> (T[7, Kz, Ky, Kx], ranks[7, 3])."""
+    Kx, Ky, Kz = (int(v) for v in K)
+    T = np.empty((7, Kz, Ky, Kx))
+    r = np.zeros(21, np.int32)
+    _check_host(lib().svh_toeplitz_store_read(os.fsencode(path), Kx, Ky, Kz, _dp(T), _i32p(r)),
+                "svh_toeplitz_store_read")
+    return T, r.reshape(7, 3)
+
+
 def host_tucker_svd(O, tol):
     """Algorithm 1 on O[D3, D2, D1] (mode 1 = last axis) -> (core[d3,d2,d1], [F1, F2, F3])."""
     O = np.ascontiguousarray(O, np.float64)
@@ -291,6 +318,10 @@ class Handle:
         return out.reshape(K, 6)
 
     # -------------------------------------------------------- kernels
+    def load_toeplitz_store(self, path):
+        """Kernels from an Algorithm 2 store (cropped to this grid)."""
+        self._ck(lib().svh_load_toeplitz_store(self._h, os.fsencode(path)), "svh_load_toeplitz_store")
+
     def generate_toeplitz(self):
         self._ck(lib().svh_generate_toeplitz(self._h), "svh_generate_toeplitz")
 
@@ -434,11 +465,17 @@ class Handle:
     def autotune(self, nb):
         """Time every FP32 tile variant of the five FFT passes for nb items, then the
         fused y/z/y path against the separate passes, and keep the fastest
-        -> (variants[6], ms per launch[6]); variants[5]: 0 fused, 1 separate."""
+        -> (variants[6], ms per launch[6]); variants[5]: 0 separate passes, 1 fused."""
         v = np.zeros(6, np.int32)
         ms = np.zeros(6)
         self._ck(lib().svh_autotune(self._h, int(nb), _i32p(v), _dp(ms)), "svh_autotune")
         return v, ms
+
+    def device_status(self, clear=True):
+        """Status word set by kernels whose bounded waits expired (0: none)."""
+        st = C.c_int32()
+        self._ck(lib().svh_get_device_status(self._h, C.byref(st), int(clear)), "svh_get_device_status")
+        return st.value
 
     def set_pass_variant(self, p, v):
         self._ck(lib().svh_set_pass_variant(self._h, int(p), int(v)), "svh_set_pass_variant")

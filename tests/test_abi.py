@@ -81,3 +81,26 @@ def test_host_tucker_matches_oracle(svh):
                 assert core.shape[::-1] == Co.shape
             for f in F:
                 assert np.allclose(f.T @ f, np.eye(f.shape[1]), atol=1e-10)
+
+
+def test_toeplitz_store_crop_and_errors(svh, tmp_path):
+    """Algorithm 2: the stored large-domain tensors, restored and cropped, give the
+    small domain's tensors (T_u depends only on the offset) within the Tucker bound."""
+    big = gr.toeplitz_octant(14, 12, 6)
+    path = str(tmp_path / "unit.svhstore")
+    tol = 1e-9
+    svh.toeplitz_store_write(path, (14, 12, 6), tol, T=big)
+    small = gr.toeplitz_octant(9, 7, 4)
+    T, ranks = svh.toeplitz_store_read(path, (9, 7, 4))
+    assert ranks.shape == (7, 3) and np.all(ranks >= 1) and np.all(ranks <= [14, 12, 6])
+    for u in range(7):
+        assert np.linalg.norm(T[u] - small[u]) <= tol * np.linalg.norm(big[u])
+    Tfull, _ = svh.toeplitz_store_read(path, (14, 12, 6))
+    for u in range(7):
+        assert np.linalg.norm(Tfull[u] - big[u]) <= tol * np.linalg.norm(big[u])
+    with pytest.raises(svh.SVHError):
+        svh.toeplitz_store_read(path, (15, 12, 6))          # larger than the stored domain
+    bad = tmp_path / "bad.svhstore"
+    bad.write_bytes(b"not a store" * 8)
+    with pytest.raises(svh.SVHError):
+        svh.toeplitz_store_read(str(bad), (4, 4, 4))

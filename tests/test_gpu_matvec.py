@@ -221,8 +221,8 @@ def test_meander_256x256x8_full_size():
         assert rel_err(y64[b], yref[b]) <= FP64_TOL
     y32 = h.matvec(om, torch.from_numpy(x.astype(np.complex64)).cuda()).cpu().numpy().astype(np.complex128)
     _check_fp32(y32, yref)
-    assert h.pass_variants()[0][5] == 2          # the fused y/z/y path applies (and ran above)
-    h.set_pass_variant(5, 1)                     # separate y, z, y passes
+    assert h.pass_variants()[0][5] == 2          # the fused y/z/y path applies
+    h.set_pass_variant(5, 1)                     # fused y/z/y (the separate passes ran above)
     y32s = h.matvec(om, torch.from_numpy(x.astype(np.complex64)).cuda()).cpu().numpy().astype(np.complex128)
     _check_fp32(y32s, yref)
     h.close()
@@ -277,14 +277,17 @@ def test_every_tile_variant_and_autotune(seed, shape, fused):
     counts, chosen = h.pass_variants()
     assert np.all(counts[:5] >= 2) and np.all(chosen == 0)
     assert counts[5] == (2 if fused else 1)
-    _check_fp32(h.matvec(om, xd).cpu().numpy().astype(np.complex128), yref)   # default path
+    _check_fp32(h.matvec(om, xd).cpu().numpy().astype(np.complex128), yref)   # default: separate passes
     if fused:
-        h.set_pass_variant(5, 1)                                                # separate passes
+        h.set_pass_variant(5, 1)                                                # fused y/z/y
+        _check_fp32(h.matvec(om, xd).cpu().numpy().astype(np.complex128), yref)
+        h.set_pass_variant(5, 0)
     for p in range(5):
         for v in range(counts[p]):
             h.set_pass_variant(p, v)
             y = h.matvec(om, xd).cpu().numpy().astype(np.complex128)
             _check_fp32(y, yref)
+            assert h.device_status() == 0          # no bounded wait (TMA z pass) expired
         h.set_pass_variant(p, 0)
     h.set_pass_variant(5, 0)
     with pytest.raises(Exception):
@@ -299,4 +302,28 @@ def test_every_tile_variant_and_autotune(seed, shape, fused):
     y64 = h.matvec(om, torch.from_numpy(x).cuda()).cpu().numpy()
     for b in range(nb):
         assert rel_err(y64[b], yref[b]) <= FP64_TOL
+    h.close()
+
+
+def test_toeplitz_store_from_device_quadrature(tmp_path):
+    """Algorithm 2 end to end: store computed by the device quadrature for a larger
+    domain, cropped to a structure's grid at set-up; the FP64 product matches the oracle's
+    (own quadrature, exact crop) within the Tucker tolerance."""
+    torch = _torch()
+    from paper_2105_08627_gb300 import build, svh
+    build.build()
+    path = str(tmp_path / "unit.svhstore")
+    svh.toeplitz_store_write(path, (40, 36, 10), 1e-11)
+    s = S.random_blob(71, 24, 20, 6, fill=0.5)
+    g, S7, P, T = oracle_reference(s)
+    h = svh.Handle(0, torch.cuda.current_stream().cuda_stream)
+    h.setup_structure(s)
+    h.load_toeplitz_store(path)
+    om = 2 * np.pi * 1e9
+    x = S.random_complex(71, (2, g.N))
+    y = h.matvec(om, torch.from_numpy(x).cuda()).cpu().numpy()
+    for b in range(2):
+        assert rel_err(y[b], op.apply_K_fft(g, S7, x[b], om, P)) <= 1e-9
+    Tst, _ = svh.toeplitz_store_read(path, (24, 20, 6))
+    assert np.abs(Tst - T).max() <= 1e-9 * np.abs(T).max()
     h.close()
