@@ -290,16 +290,20 @@ int svh_matvec_noalloc(svh_handle* h, double omega, int nb, const void* x_dev, v
  * or full z pencils). Choice 5 is the path: 0 runs the passes separately,
  * 1 fuses passes 1-3 into one kernel per (kx, item) that keeps the column's
  * (basis, plane, y) slab in shared memory (offered when it fits and the
- * active planes are contiguous). svh_autotune times every variant of every pass on
- * this handle's grid for nb right-hand sides (zero data, 5 launches each,
- * CUDA events on the handle's stream), then the fused path against the
- * separate passes, and keeps the fastest for later FP32 products; results
- * are cached per process for equal grids and nb. variants[6] and ms[6] (may
- * be NULL) receive the choices and their milliseconds per launch. svh_set_pass_variant forces one (SVH_ERR_ARG if
+ * active planes are contiguous). Choice 6 is the stream schedule of a
+ * product: 0 runs the Tucker restore and the node rows on the handle's second
+ * stream, overlapping passes 1-2; 1 overlaps only the node rows; 2 uses one
+ * stream. svh_autotune times every variant of every pass on this handle's
+ * grid for nb right-hand sides (zero data, 5 launches each, CUDA events on
+ * the handle's stream), then the fused path against the separate passes,
+ * then the three schedules on whole products, and keeps the fastest for
+ * later FP32 products; results are cached per process for equal grids and
+ * nb. variants[7] and ms[7] (may be NULL) receive the choices and their
+ * milliseconds per launch. svh_set_pass_variant forces one (SVH_ERR_ARG if
  * the pass has no such variant at this size); svh_get_pass_variants reports
  * the number of variants per pass (0: generic kernel) and the current choice.
  * FP64 products always use variant 0. */
-#define SVH_NFFTPASS 6
+#define SVH_NFFTPASS 7
 /* Device status word of the handle: bit 0 (SVH_STATUS_TMA_TIMEOUT) is set
  * when a kernel's bounded wait for a TMA copy expired (its results are then
  * invalid). clear != 0 resets it. */
@@ -309,10 +313,13 @@ int svh_autotune(svh_handle* h, int nb, int32_t* variants, double* ms);
 int svh_set_pass_variant(svh_handle* h, int pass, int variant);
 int svh_get_pass_variants(const svh_handle* h, int32_t* counts, int32_t* chosen);
 
-/* ---- Per-pass timing of svh_matvec with CUDA events on the handle's stream.
+/* ---- Per-pass timing of svh_matvec with CUDA events (begin and end of each
+ * pass on the stream it runs on).
  * Passes: 0 Tucker rebuild (Eq. 10), 1 x-forward with gather, 2 y-forward,
  * 3 z-FFT + block multiply + inverse z-FFT, 4 y-inverse, 5 x-inverse with
- * the diagonal and A^T epilogue, 6 node rows (A I). svh_profile_begin
+ * the diagonal and A^T epilogue, 6 node rows (A I). Passes 0 and 6 run on
+ * the handle's second stream, overlapping passes 1-2 (the sum of the pass
+ * times can exceed the call's duration). svh_profile_begin
  * starts recording for up to max_calls matvec calls (events are recorded
  * without synchronising); svh_profile_end waits for them and returns the
  * summed milliseconds per pass in ms[SVH_NPASS] and the calls recorded. */

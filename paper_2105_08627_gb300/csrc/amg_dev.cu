@@ -12,7 +12,9 @@
 //   * the K-cycle's Krylov acceleration always takes both inner steps (the
 //     host version skips the second when the first reduced the residual 4x),
 //     so nothing waits for the host; the 2 x 2 Galerkin combination falls back
-//     to the first step when the second adds nothing;
+//     to the first step when the second adds nothing; levels below 8000
+//     unknowns take one plain cycle (their launches are latency-bound and
+//     the two steps would double the visits of every level below);
 //   * smoothing, residual and restriction are one kernel (pre), and
 //     prolongation, residual and the second smoothing sweep another (post);
 //     the right-hand side b - a1 w1 and the coarse correction c1 v1 + c2 v2
@@ -33,10 +35,11 @@ namespace svh {
 namespace {
 
 constexpr int TPB = 256;
+constexpr int kKrylovMinRows = 8000;   // levels below this size take one plain cycle
 
 __device__ __forceinline__ double2 d2(double x, double y) { return make_double2(x, y); }
 __device__ __forceinline__ double2 add(double2 a, double2 b) { return d2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ double2 sub(double2 a, double2 b) { return d2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 sub2(double2 a, double2 b) { return d2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ double2 mul(double2 a, double2 b) { return d2(a.x * b.x, a.y * b.y); }
 __device__ __forceinline__ double2 scl(double s, double2 a) { return d2(s * a.x, s * a.y); }
 
@@ -49,7 +52,7 @@ struct VRef {
 
 __device__ __forceinline__ double2 vget(const VRef& B, int64_t off, double2 cf) {
     double2 v = B.b[off];
-    if (B.w) v = sub(v, mul(cf, B.w[off]));
+    if (B.w) v = sub2(v, mul(cf, B.w[off]));
     return v;
 }
 
@@ -129,28 +132,47 @@ __device__ bool block_sums_last(double2 (&val)[ND], double2* part, unsigned* cnt
     return true;
 }
 
+// Sparse rows are processed by groups of G lanes (G = 1 .. 32: one lane per
+// row on the large fine levels, more on the small coarse levels with long
+// Galerkin rows): lane `sub` of a group takes the row's entries
+// sub, sub + G, ...; the group's partial sums meet in one shuffle reduction
+// after the loops (every lane reaches it, so the shuffles stay convergent).
+template <int G>
+__device__ __forceinline__ double2 group_sum(double2 v) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) {
+        v.x += __shfl_down_sync(0xffffffffu, v.x, o, G);
+        v.y += __shfl_down_sync(0xffffffffu, v.y, o, G);
+    }
+    return v;   // complete in the group's lane 0
+}
+
 // K-cycle, first half: x0 = b / l1 (one l1-Jacobi sweep from zero), the
-// residual b - A x0 and its restriction to the aggregates (sum over each).
-__global__ void k_kc_pre(int n, int nc, const int* __restrict__ rp, const int* __restrict__ ci,
-                         const double* __restrict__ v, const double* __restrict__ l1inv,
-                         const int* __restrict__ crp, const int* __restrict__ cidx, VRef B,
-                         double2* __restrict__ rc) {
+// residual b - A x0 and its restriction to the aggregates (sum over each);
+// one group per aggregate.
+template <int G>
+__global__ void __launch_bounds__(TPB) k_kc_pre(int n, int nc, const int* __restrict__ rp, const int* __restrict__ ci,
+                                                const double* __restrict__ v, const double* __restrict__ l1inv,
+                                                const int* __restrict__ crp, const int* __restrict__ cidx, VRef B,
+                                                double2* __restrict__ rc) {
     const int r = blockIdx.y;
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= nc) return;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = (int)(t / G), sub = (int)(t % G);
     const int64_t off = (int64_t)r * n;
     const double2 cf = B.w ? B.coef[r] : d2(0, 0);
     double2 s = d2(0, 0);
-    for (int p = crp[c]; p < crp[c + 1]; ++p) {
-        const int i = cidx[p];
-        double2 ax = d2(0, 0);
-        for (int q = rp[i]; q < rp[i + 1]; ++q) {
-            const int j = ci[q];
-            ax = add(ax, scl(v[q] * l1inv[j], vget(B, off + j, cf)));
+    if (c < nc) {
+        for (int p = crp[c]; p < crp[c + 1]; ++p) {
+            const int i = cidx[p];
+            if (sub == 0) s = add(s, vget(B, off + i, cf));
+            for (int q = rp[i] + sub; q < rp[i + 1]; q += G) {
+                const int j = ci[q];
+                s = sub2(s, scl(v[q] * l1inv[j], vget(B, off + j, cf)));
+            }
         }
-        s = add(s, sub(vget(B, off + i, cf), ax));
     }
-    rc[(int64_t)r * nc + c] = s;
+    s = group_sum<G>(s);
+    if (c < nc && sub == 0) rc[(int64_t)r * nc + c] = s;
 }
 
 __device__ __forceinline__ double2 xcget(const XRef& X, int64_t off, int r) {
@@ -159,24 +181,31 @@ __device__ __forceinline__ double2 xcget(const XRef& X, int64_t off, int r) {
 }
 
 // K-cycle, second half: x1 = b / l1 + P xc (coarse correction), then one more
-// l1-Jacobi sweep x = x1 + (b - A x1) / l1.
-__global__ void k_kc_post(int n, int nc, const int* __restrict__ rp, const int* __restrict__ ci,
-                          const double* __restrict__ v, const double* __restrict__ l1inv,
-                          const int* __restrict__ agg, VRef B, XRef XC, double2* __restrict__ X) {
+// l1-Jacobi sweep x = x1 + (b - A x1) / l1; one group per row.
+template <int G>
+__global__ void __launch_bounds__(TPB) k_kc_post(int n, int nc, const int* __restrict__ rp, const int* __restrict__ ci,
+                                                 const double* __restrict__ v, const double* __restrict__ l1inv,
+                                                 const int* __restrict__ agg, VRef B, XRef XC,
+                                                 double2* __restrict__ X) {
     const int r = blockIdx.y;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = (int)(t / G), sub = (int)(t % G);
     const int64_t off = (int64_t)r * n, offc = (int64_t)r * nc;
     const double2 cf = B.w ? B.coef[r] : d2(0, 0);
     double2 ax = d2(0, 0);
-    for (int q = rp[i]; q < rp[i + 1]; ++q) {
-        const int j = ci[q];
-        const double2 xj = add(scl(l1inv[j], vget(B, off + j, cf)), xcget(XC, offc + agg[j], r));
-        ax = add(ax, scl(v[q], xj));
+    if (i < n) {
+        for (int q = rp[i] + sub; q < rp[i + 1]; q += G) {
+            const int j = ci[q];
+            const double2 xj = add(scl(l1inv[j], vget(B, off + j, cf)), xcget(XC, offc + agg[j], r));
+            ax = add(ax, scl(v[q], xj));
+        }
     }
-    const double2 bi = vget(B, off + i, cf);
-    const double2 xi = add(scl(l1inv[i], bi), xcget(XC, offc + agg[i], r));
-    X[off + i] = add(xi, scl(l1inv[i], sub(bi, ax)));
+    ax = group_sum<G>(ax);
+    if (i < n && sub == 0) {
+        const double2 bi = vget(B, off + i, cf);
+        const double2 xi = add(scl(l1inv[i], bi), xcget(XC, offc + agg[i], r));
+        X[off + i] = add(xi, scl(l1inv[i], sub2(bi, ax)));
+    }
 }
 
 // coarsest level: X = C^{-1} b, one warp per row
@@ -206,22 +235,25 @@ __global__ void k_dense(int n, const double* __restrict__ cinv, const double2* _
 // w = A vin with dot products; MODE 1 (first Krylov step): d11 = v1.w,
 // g1 = v1.b -> a1 = g1 / d11. MODE 2 (second): d12 = v1.w, d22 = v2.w,
 // g2 = v2.b -> (c1, c2) minimising the A-norm of the error over span{v1, v2}.
-template <int MODE>
+template <int MODE, int G>
 __global__ void __launch_bounds__(TPB) k_kc_spmv(int n, const int* __restrict__ rp, const int* __restrict__ ci,
                                                  const double* __restrict__ v, const double2* __restrict__ vin,
                                                  const double2* __restrict__ v1, const double2* __restrict__ b,
                                                  double2* __restrict__ w, double2* part, unsigned* cnt, double2* sc,
                                                  int nrhs) {
     const int r = blockIdx.y;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = (int)(t / G), sub = (int)(t % G);
     const int64_t off = (int64_t)r * n;
     constexpr int ND = MODE == 1 ? 2 : 3;
     double2 val[ND];
 #pragma unroll
     for (int k = 0; k < ND; ++k) val[k] = d2(0, 0);
-    if (i < n) {
-        double2 ax = d2(0, 0);
-        for (int q = rp[i]; q < rp[i + 1]; ++q) ax = add(ax, scl(v[q], vin[off + ci[q]]));
+    double2 ax = d2(0, 0);
+    if (i < n)
+        for (int q = rp[i] + sub; q < rp[i + 1]; q += G) ax = add(ax, scl(v[q], vin[off + ci[q]]));
+    ax = group_sum<G>(ax);
+    if (i < n && sub == 0) {
         w[off + i] = ax;
         const double2 vi = vin[off + i], bi = b[off + i];
         if (MODE == 1) {
@@ -312,21 +344,25 @@ __global__ void k_fcg_dir(int64_t n, const double2* __restrict__ z, const double
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int64_t o = r * n + i;
-    p[o] = first ? z[o] : sub(z[o], mul(fs[F_BETA * nrhs + r], pold[o]));
+    p[o] = first ? z[o] : sub2(z[o], mul(fs[F_BETA * nrhs + r], pold[o]));
 }
 
 // q = S p, pq = p.q, alpha = (p.r) / pq for the active systems (0 for the others)
+template <int G>
 __global__ void __launch_bounds__(TPB) k_fcg_spmv(int n, const int* __restrict__ rp, const int* __restrict__ ci,
                                                   const double* __restrict__ v, const double2* __restrict__ p,
                                                   const double2* __restrict__ rr, double2* __restrict__ q,
                                                   double2* part, unsigned* cnt, double2* fs, int nrhs) {
     const int r = blockIdx.y;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = (int)(t / G), sub = (int)(t % G);
     const int64_t off = (int64_t)r * n;
     double2 val[2] = {d2(0, 0), d2(0, 0)};
-    if (i < n) {
-        double2 ax = d2(0, 0);
-        for (int k = rp[i]; k < rp[i + 1]; ++k) ax = add(ax, scl(v[k], p[off + ci[k]]));
+    double2 ax = d2(0, 0);
+    if (i < n)
+        for (int k = rp[i] + sub; k < rp[i + 1]; k += G) ax = add(ax, scl(v[k], p[off + ci[k]]));
+    ax = group_sum<G>(ax);
+    if (i < n && sub == 0) {
         q[off + i] = ax;
         const double2 pi = p[off + i];
         val[0] = mul(pi, ax);
@@ -353,7 +389,7 @@ __global__ void __launch_bounds__(TPB) k_fcg_update(int n, const double2* __rest
     double2 val[1] = {d2(0, 0)};
     if (i < n) {
         const double2 xi = add(x[off + i], mul(alpha, p[off + i]));
-        const double2 ri = sub(rr[off + i], mul(alpha, q[off + i]));
+        const double2 ri = sub2(rr[off + i], mul(alpha, q[off + i]));
         x[off + i] = xi;
         rr[off + i] = ri;
         val[0] = mul(ri, ri);
@@ -375,6 +411,8 @@ __global__ void __launch_bounds__(TPB) k_fcg_update(int n, const double2* __rest
 // ---- device copy of one hierarchy
 struct DLevel {
     int n = 0, nc = 0;
+    int g = 1, gp = 1;           // lanes per row (SpMV kernels) and per aggregate (restriction)
+    bool krylov = true;          // coarse solves on this level take the two Krylov steps
     DevBuf rp, ci, v, l1inv, agg, crp, cidx;
     DevBuf v1, w1, v2, w2, rc;   // [nrhs][n] (rc: [nrhs][nc])
     DevBuf sc, part, cnt;        // scalar slots, block partials, completion counters
@@ -410,6 +448,15 @@ struct DevAmg {
 
 unsigned nblk(int64_t n) { return (unsigned)((n + TPB - 1) / TPB); }
 
+// lanes per unit (row or aggregate) for `units` units of `per` entries on average:
+// one lane per unit while the units alone fill the GPU (~160 K threads), more on
+// the small coarse levels (whose Galerkin rows are long), at most one per entry
+int lanes_for(int64_t units, double per) {
+    int g = 1;
+    while (g < 32 && g < per && (int64_t)g * units < 160000) g *= 2;
+    return g;
+}
+
 template <typename T>
 T* P(DevBuf& b) { return static_cast<T*>(b.p); }
 
@@ -425,6 +472,11 @@ int upload(Handle* h, DevAmg& D, const AmgView& A) {
         L.n = V.n;
         L.nc = l + 1 < nl ? V.nc : 0;
         const int nnz = V.rp[V.n];
+        L.g = lanes_for(V.n, (double)nnz / std::max(1, V.n));
+        // the K-cycle's two Krylov steps double the visits of every level below; on the
+        // small levels (latency-bound launches) one cycle is cheaper overall
+        L.krylov = V.n >= kKrylovMinRows;
+        L.gp = L.nc > 0 ? lanes_for(L.nc, (double)nnz / L.nc) : 1;
         std::vector<double> inv(V.n);
         for (int i = 0; i < V.n; ++i) inv[i] = 1.0 / V.l1[i];
         int rc;
@@ -469,7 +521,7 @@ int ensure_work(Handle* h, DevAmg& D, int nrhs) {
         if ((rc = dev_alloc(h, L.v1, vb)) || (rc = dev_alloc(h, L.w1, vb)) || (rc = dev_alloc(h, L.v2, vb)) ||
             (rc = dev_alloc(h, L.w2, vb)) || (rc = dev_alloc(h, L.rc, (size_t)nrhs * (L.nc > 0 ? L.nc : 1) * 16)) ||
             (rc = dev_alloc(h, L.sc, (size_t)NSLOT * nrhs * 16)) ||
-            (rc = dev_alloc(h, L.part, (size_t)nrhs * nblk(L.n) * 3 * 16)) ||
+            (rc = dev_alloc(h, L.part, (size_t)nrhs * nblk((int64_t)L.n * L.g) * 3 * 16)) ||
             (rc = dev_alloc(h, L.cnt, (size_t)nrhs * 4)))
             return rc;
         SVH_CUDA_TRY(h, cudaMemsetAsync(L.cnt.p, 0, (size_t)nrhs * 4, D.st));
@@ -479,7 +531,8 @@ int ensure_work(Handle* h, DevAmg& D, int nrhs) {
     if ((rc = dev_alloc(h, D.fx, vb)) || (rc = dev_alloc(h, D.fr, vb)) || (rc = dev_alloc(h, D.fz, vb)) ||
         (rc = dev_alloc(h, D.fp, vb)) || (rc = dev_alloc(h, D.fq, vb)) || (rc = dev_alloc(h, D.fpo, vb)) ||
         (rc = dev_alloc(h, D.fqo, vb)) || (rc = dev_alloc(h, D.fs, (size_t)NFSLOT * nrhs * 16)) ||
-        (rc = dev_alloc(h, D.fpart, (size_t)nrhs * nblk(D.lv[0].n) * 2 * 16)) || (rc = dev_alloc(h, D.fcnt, (size_t)nrhs * 4)))
+        (rc = dev_alloc(h, D.fpart, (size_t)nrhs * std::max(nblk((int64_t)D.lv[0].n * D.lv[0].g), nblk(D.lv[0].n)) * 2 * 16)) ||
+        (rc = dev_alloc(h, D.fcnt, (size_t)nrhs * 4)))
         return rc;
     SVH_CUDA_TRY(h, cudaMemsetAsync(D.fcnt.p, 0, (size_t)nrhs * 4, D.st));
     if (D.host_fs) cudaFreeHost(D.host_fs);
@@ -491,6 +544,49 @@ int ensure_work(Handle* h, DevAmg& D, int nrhs) {
 
 void kcycle(Handle* h, DevAmg& D, int l, VRef B, double2* X, int nrhs);
 
+template <int G>
+void launch_pre(DLevel& L, VRef B, int nrhs, cudaStream_t s) {
+    k_kc_pre<G><<<dim3(nblk((int64_t)L.nc * G), nrhs), TPB, 0, s>>>(L.n, L.nc, P<int>(L.rp), P<int>(L.ci),
+                                                                   P<double>(L.v), P<double>(L.l1inv), P<int>(L.crp),
+                                                                   P<int>(L.cidx), B, P<double2>(L.rc));
+}
+
+template <int G>
+void launch_post(DLevel& L, VRef B, XRef XC, double2* X, int nrhs, cudaStream_t s) {
+    k_kc_post<G><<<dim3(nblk((int64_t)L.n * G), nrhs), TPB, 0, s>>>(L.n, L.nc, P<int>(L.rp), P<int>(L.ci),
+                                                                    P<double>(L.v), P<double>(L.l1inv), P<int>(L.agg),
+                                                                    B, XC, X);
+}
+
+template <int MODE, int G>
+void launch_spmv_kc(DLevel& L, const double2* vin, const double2* v1, const double2* b, double2* w, int nrhs,
+                    cudaStream_t s) {
+    k_kc_spmv<MODE, G><<<dim3(nblk((int64_t)L.n * G), nrhs), TPB, 0, s>>>(
+        L.n, P<int>(L.rp), P<int>(L.ci), P<double>(L.v), vin, v1, b, w, P<double2>(L.part), P<unsigned>(L.cnt),
+        P<double2>(L.sc), nrhs);
+}
+
+template <int MODE>
+void spmv_kc(DLevel& L, const double2* vin, const double2* v1, const double2* b, double2* w, int nrhs,
+             cudaStream_t s) {
+    switch (L.g) {
+        case 1: launch_spmv_kc<MODE, 1>(L, vin, v1, b, w, nrhs, s); break;
+        case 2: launch_spmv_kc<MODE, 2>(L, vin, v1, b, w, nrhs, s); break;
+        case 4: launch_spmv_kc<MODE, 4>(L, vin, v1, b, w, nrhs, s); break;
+        case 8: launch_spmv_kc<MODE, 8>(L, vin, v1, b, w, nrhs, s); break;
+        case 16: launch_spmv_kc<MODE, 16>(L, vin, v1, b, w, nrhs, s); break;
+        default: launch_spmv_kc<MODE, 32>(L, vin, v1, b, w, nrhs, s); break;
+    }
+}
+
+template <int G>
+void launch_fcg_spmv(DLevel& L0, const double2* p, const double2* r, double2* q, DevAmg& D, int nrhs,
+                     cudaStream_t s) {
+    k_fcg_spmv<G><<<dim3(nblk((int64_t)L0.n * G), nrhs), TPB, 0, s>>>(L0.n, P<int>(L0.rp), P<int>(L0.ci),
+                                                                      P<double>(L0.v), p, r, q, P<double2>(D.fpart),
+                                                                      P<unsigned>(D.fcnt), P<double2>(D.fs), nrhs);
+}
+
 // two Krylov steps on level l with the level-l cycle as preconditioner; the
 // result is c1 v1 + c2 v2 of this level (read by the caller's post kernel),
 // or v1 alone on the coarsest level
@@ -501,14 +597,14 @@ void coarse_krylov(Handle* h, DevAmg& D, int l, const double2* b, int nrhs) {
         k_dense<<<dim3((L.n + 7) / 8, nrhs), 256, 0, s>>>(L.n, P<double>(D.cinv), b, P<double2>(L.v1));
         return;
     }
+    if (!L.krylov) {   // small level: one cycle, no Krylov acceleration (result in v1)
+        kcycle(h, D, l, VRef{b, nullptr, nullptr}, P<double2>(L.v1), nrhs);
+        return;
+    }
     kcycle(h, D, l, VRef{b, nullptr, nullptr}, P<double2>(L.v1), nrhs);
-    k_kc_spmv<1><<<dim3(nblk(L.n), nrhs), TPB, 0, s>>>(L.n, P<int>(L.rp), P<int>(L.ci), P<double>(L.v),
-                                                        P<double2>(L.v1), nullptr, b, P<double2>(L.w1),
-                                                        P<double2>(L.part), P<unsigned>(L.cnt), P<double2>(L.sc), nrhs);
+    spmv_kc<1>(L, P<double2>(L.v1), nullptr, b, P<double2>(L.w1), nrhs, s);
     kcycle(h, D, l, VRef{b, P<double2>(L.w1), P<double2>(L.sc) + S_A1 * nrhs}, P<double2>(L.v2), nrhs);
-    k_kc_spmv<2><<<dim3(nblk(L.n), nrhs), TPB, 0, s>>>(L.n, P<int>(L.rp), P<int>(L.ci), P<double>(L.v),
-                                                        P<double2>(L.v2), P<double2>(L.v1), b, P<double2>(L.w2),
-                                                        P<double2>(L.part), P<unsigned>(L.cnt), P<double2>(L.sc), nrhs);
+    spmv_kc<2>(L, P<double2>(L.v2), P<double2>(L.v1), b, P<double2>(L.w2), nrhs, s);
 }
 
 // X ~= A_l^{-1} B (zero initial guess), l below the coarsest level
@@ -516,17 +612,28 @@ void kcycle(Handle* h, DevAmg& D, int l, VRef B, double2* X, int nrhs) {
     DLevel& L = D.lv[l];
     DLevel& C = D.lv[l + 1];
     cudaStream_t s = D.st;
-    k_kc_pre<<<dim3(nblk(L.nc), nrhs), TPB, 0, s>>>(L.n, L.nc, P<int>(L.rp), P<int>(L.ci), P<double>(L.v),
-                                                     P<double>(L.l1inv), P<int>(L.crp), P<int>(L.cidx), B,
-                                                     P<double2>(L.rc));
+    switch (L.gp) {
+        case 1: launch_pre<1>(L, B, nrhs, s); break;
+        case 2: launch_pre<2>(L, B, nrhs, s); break;
+        case 4: launch_pre<4>(L, B, nrhs, s); break;
+        case 8: launch_pre<8>(L, B, nrhs, s); break;
+        case 16: launch_pre<16>(L, B, nrhs, s); break;
+        default: launch_pre<32>(L, B, nrhs, s); break;
+    }
     coarse_krylov(h, D, l + 1, P<double2>(L.rc), nrhs);
     XRef XC{P<double2>(C.v1), P<double2>(C.v2), nullptr, nullptr};
-    if (l + 2 < (int)D.lv.size()) {
+    if (l + 2 < (int)D.lv.size() && C.krylov) {
         XC.c1 = P<double2>(C.sc) + S_C1 * nrhs;
         XC.c2 = P<double2>(C.sc) + S_C2 * nrhs;
     }
-    k_kc_post<<<dim3(nblk(L.n), nrhs), TPB, 0, s>>>(L.n, L.nc, P<int>(L.rp), P<int>(L.ci), P<double>(L.v),
-                                                     P<double>(L.l1inv), P<int>(L.agg), B, XC, X);
+    switch (L.g) {
+        case 1: launch_post<1>(L, B, XC, X, nrhs, s); break;
+        case 2: launch_post<2>(L, B, XC, X, nrhs, s); break;
+        case 4: launch_post<4>(L, B, XC, X, nrhs, s); break;
+        case 8: launch_post<8>(L, B, XC, X, nrhs, s); break;
+        case 16: launch_post<16>(L, B, XC, X, nrhs, s); break;
+        default: launch_post<32>(L, B, XC, X, nrhs, s); break;
+    }
 }
 
 }  // namespace
@@ -577,8 +684,14 @@ int precond_schur_solve_dev(Handle* h, int nb, int per_freq, const void* e_dev, 
             if (it > 0)
                 k_fcg_beta<<<dim3(g, nrhs), TPB, 0, s>>>(n, z, qo, P<double2>(D.fpart), P<unsigned>(D.fcnt), fs, nrhs);
             k_fcg_dir<<<dim3(g, nrhs), TPB, 0, s>>>(n, z, po, p, fs, nrhs, it == 0);
-            k_fcg_spmv<<<dim3(g, nrhs), TPB, 0, s>>>(n, P<int>(L0.rp), P<int>(L0.ci), P<double>(L0.v), p, r, q,
-                                                      P<double2>(D.fpart), P<unsigned>(D.fcnt), fs, nrhs);
+            switch (L0.g) {
+                case 1: launch_fcg_spmv<1>(L0, p, r, q, D, nrhs, s); break;
+                case 2: launch_fcg_spmv<2>(L0, p, r, q, D, nrhs, s); break;
+                case 4: launch_fcg_spmv<4>(L0, p, r, q, D, nrhs, s); break;
+                case 8: launch_fcg_spmv<8>(L0, p, r, q, D, nrhs, s); break;
+                case 16: launch_fcg_spmv<16>(L0, p, r, q, D, nrhs, s); break;
+                default: launch_fcg_spmv<32>(L0, p, r, q, D, nrhs, s); break;
+            }
             k_fcg_update<<<dim3(g, nrhs), TPB, 0, s>>>(n, p, q, x, r, P<double2>(D.fpart), P<unsigned>(D.fcnt), fs,
                                                         nrhs, tol2);
         };

@@ -350,6 +350,30 @@ void matvec_scratch_bytes(const Handle* h, int nb, int precision, size_t* b1, si
     *b2 = (size_t)nb * 5 * nza * (size_t)h->Py * h->Px * csz;
 }
 
+// the product's second stream and its fork / join events (created on first use)
+static int ensure_aux(Handle* h) {
+    if (h->aux) return SVH_OK;
+    SVH_CUDA_TRY(h, cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking));
+    SVH_CUDA_TRY(h, cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+    SVH_CUDA_TRY(h, cudaEventCreateWithFlags(&h->ev_spec, cudaEventDisableTiming));
+    SVH_CUDA_TRY(h, cudaEventCreateWithFlags(&h->ev_done, cudaEventDisableTiming));
+    SVH_CUDA_TRY(h, cudaEventCreateWithFlags(&h->ev_x, cudaEventDisableTiming));
+    return SVH_OK;
+}
+
+int matvec_prefork(Handle* h) {
+    if (int rc = ensure_aux(h)) return rc;
+    SVH_CUDA_TRY(h, cudaEventRecord(h->ev_fork, h->stream));
+    SVH_CUDA_TRY(h, cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
+    h->preforked = true;
+    return SVH_OK;
+}
+
+int matvec_mark_input_ready(Handle* h) {
+    SVH_CUDA_TRY(h, cudaEventRecord(h->ev_x, h->stream));
+    return SVH_OK;
+}
+
 static void ensure_smem_optin(Handle* h) {
     if (h->smem_optin == 0) {
         int v = 0;
@@ -427,72 +451,114 @@ static int run_matvec(Handle* h, double omega, const double* d_omegas, int nb, c
     const int32_t* rows = static_cast<const int32_t*>(h->d_rows.p);
     const uint8_t* d_rowmask = static_cast<const uint8_t*>(h->d_rowmask.p);
     PassArgs pa = pass_args<T>(h, omega, d_omegas, nb, x, y, masked, B1, B2);
-    prof_mark(h, -1);
     // the fused y/z/y path (FP32) when the slab fits shared memory and the tile choice allows it
     ensure_smem_optin(h);
     const bool fused = ti == 0 && h->tune32[5] == 1 && fused_path_ok(pa, h->smem_optin);
-    // pass 3 needs the spectra: rebuild them from Tucker first when asked (Eq. 10)
-    if (allow_rebuild && ti == 0 && h->kernel_mode == SVH_KERNELS_TUCKER_REBUILD) {
-        int rc = launch_tucker_rebuild(h);
-        if (rc) return rc;
+    const bool rebuild = allow_rebuild && ti == 0 && h->kernel_mode == SVH_KERNELS_TUCKER_REBUILD;
+    cudaStream_t s = h->stream, sa = nullptr;
+    if (int rc = ensure_aux(h)) return rc;
+    sa = h->aux;
+    // fork: the restore (needed from pass 3 on) and the node rows (independent of the
+    // FFT passes) run on the second stream while passes 1 and 2 run here; the
+    // host-buffer entry point forks before its input copy (the restore needs no input)
+    const bool preforked = h->preforked;
+    h->preforked = false;
+    if (!preforked) {
+        SVH_CUDA_TRY(h, cudaEventRecord(h->ev_fork, s));
+        SVH_CUDA_TRY(h, cudaStreamWaitEvent(sa, h->ev_fork, 0));
     }
-    prof_mark(h, 0);
+    // stream schedule (tuned): 0 restore and node rows on the second stream, 1 node rows
+    // only (restore first on this stream), 2 everything on this stream
+    // (the host-buffer entry point always overlaps the restore with its input copy)
+    const int sched = preforked ? 0 : h->tune32[6];
+    cudaStream_t s_rb = sched == 0 ? sa : s, s_nd = sched == 2 ? s : sa;
+    int rc_aux = SVH_OK;
+    prof_at(h, 0, 0, s_rb);
+    if (rebuild) rc_aux = launch_tucker_rebuild(h, s_rb);   // pass 3 needs the spectra (Eq. 10)
+    prof_at(h, 0, 1, s_rb);
+    cudaEventRecord(h->ev_spec, s_rb);
+    if (preforked && s_nd == sa) cudaStreamWaitEvent(sa, h->ev_x, 0);   // the node rows read the input
+    if (sched == 1) {   // the node rows fork after the restore
+        cudaEventRecord(h->ev_fork, s);
+        cudaStreamWaitEvent(sa, h->ev_fork, 0);
+    }
+    if (s_nd == sa) {
+        prof_at(h, 6, 0, sa);
+        int64_t n = M * nb;
+        k_nodes<T><<<(unsigned)((n + 255) / 256), 256, 0, sa>>>(
+            x, y, Nvec, K, M, nb, static_cast<const int32_t*>(h->d_ninc.p),
+            static_cast<const uint8_t*>(h->d_free.p), masked);
+        prof_at(h, 6, 1, sa);
+    }
+    cudaEventRecord(h->ev_done, sa);
     auto var = [&](int p) { return ti == 0 ? h->tune32[p] : 0; };
     if (fused) {
-        launch_x_t(pa, false, h->stream);
-        prof_mark(h, 1);
-        prof_mark(h, 2);
-        launch_yz(pa, h->smem_optin, h->stream);
-        prof_mark(h, 3);
-        prof_mark(h, 4);
-        launch_x_t(pa, true, h->stream);
-        prof_mark(h, 5);
+        prof_at(h, 1, 0, s);
+        launch_x_t(pa, false, s);
+        prof_at(h, 1, 1, s);
+        prof_at(h, 2, 0, s);
+        prof_at(h, 2, 1, s);
+        cudaStreamWaitEvent(s, h->ev_spec, 0);
+        prof_at(h, 3, 0, s);
+        launch_yz(pa, h->smem_optin, s);
+        prof_at(h, 3, 1, s);
+        prof_at(h, 4, 0, s);
+        prof_at(h, 4, 1, s);
+        prof_at(h, 5, 0, s);
+        launch_x_t(pa, true, s);
+        prof_at(h, 5, 1, s);
     } else {
         // pass 1
+        prof_at(h, 1, 0, s);
         pa.var = var(0);
-        if (!launch_x_fast<T>(pa, false, h->stream)) {
+        if (!launch_x_fast<T>(pa, false, s)) {
             int lpb = std::max(1, MAXPTS * NTHR / Px);
             int64_t nlines = (int64_t)nb * 5 * nrows;
             size_t sm = (size_t)(Px + lpb * (Px + 1)) * csz;
             cudaFuncSetAttribute(k_xfwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             dim3 grid((unsigned)((nlines + lpb - 1) / lpb));
-            k_xfwd<T><<<grid, NTHR, sm, h->stream>>>(x, Nvec, K, vidx, rows, nrows, nza, h->Kx, h->Ky, B1,
-                                                     px, twx, lpb, nlines);
+            k_xfwd<T><<<grid, NTHR, sm, s>>>(x, Nvec, K, vidx, rows, nrows, nza, h->Kx, h->Ky, B1, px, twx, lpb,
+                                             nlines);
         }
-        prof_mark(h, 1);
+        prof_at(h, 1, 1, s);
         // pass 2
+        prof_at(h, 2, 0, s);
         int tby = std::max(1, std::min(32, MAXPTS * NTHR / Py));
         pa.var = var(1);
-        if (!launch_y_fast<T>(pa, false, h->stream)) {
+        if (!launch_y_fast<T>(pa, false, s)) {
             size_t sm = (size_t)(Py + Py * tby) * csz;
             cudaFuncSetAttribute(k_ycol<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             dim3 grid((Px + tby - 1) / tby, nza, nb * 5);
-            k_ycol<T, false><<<grid, NTHR, sm, h->stream>>>(B1, B2, nza, h->Ky, Py, Px, d_rowmask, py, twy, tby);
+            k_ycol<T, false><<<grid, NTHR, sm, s>>>(B1, B2, nza, h->Ky, Py, Px, d_rowmask, py, twy, tby);
         }
-        prof_mark(h, 2);
-        // pass 3
+        prof_at(h, 2, 1, s);
+        // pass 3 (after the restore on the second stream)
+        cudaStreamWaitEvent(s, h->ev_spec, 0);
+        prof_at(h, 3, 0, s);
         pa.var = var(2);
-        if (!launch_z_fast<T>(pa, h->stream)) {
+        if (!launch_z_fast<T>(pa, s)) {
             int tbz = std::max(1, std::min(64, MAXPTS * NTHR / (5 * Pz)));
             size_t sm = (size_t)(Pz + Pz * 5 * tbz) * csz;
             cudaFuncSetAttribute(k_zpass<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             dim3 grid(nb, (Px + tbz - 1) / tbz, Py);
-            k_zpass<T><<<grid, NTHR, sm, h->stream>>>(B2, nb, nza, static_cast<const int32_t*>(h->d_zlist.p),
-                                                      Pz, Py, Px, h->Hx, h->Hy, h->Hz, spec, pz, twz, tbz);
+            k_zpass<T><<<grid, NTHR, sm, s>>>(B2, nb, nza, static_cast<const int32_t*>(h->d_zlist.p), Pz, Py, Px,
+                                              h->Hx, h->Hy, h->Hz, spec, pz, twz, tbz);
         }
-        prof_mark(h, 3);
+        prof_at(h, 3, 1, s);
         // pass 4
+        prof_at(h, 4, 0, s);
         pa.var = var(3);
-        if (!launch_y_fast<T>(pa, true, h->stream)) {
+        if (!launch_y_fast<T>(pa, true, s)) {
             size_t sm = (size_t)(Py + Py * tby) * csz;
             cudaFuncSetAttribute(k_ycol<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             dim3 grid((Px + tby - 1) / tby, nza, nb * 5);
-            k_ycol<T, true><<<grid, NTHR, sm, h->stream>>>(B2, B1, nza, h->Ky, Py, Px, d_rowmask, py, twy, tby);
+            k_ycol<T, true><<<grid, NTHR, sm, s>>>(B2, B1, nza, h->Ky, Py, Px, d_rowmask, py, twy, tby);
         }
-        prof_mark(h, 4);
+        prof_at(h, 4, 1, s);
         // pass 5 + epilogue
+        prof_at(h, 5, 0, s);
         pa.var = var(4);
-        if (!launch_x_fast<T>(pa, true, h->stream)) {
+        if (!launch_x_fast<T>(pa, true, s)) {
             int lpb = std::max(1, MAXPTS * NTHR / Px);
             int64_t nlines = (int64_t)nb * 5 * nrows;
             size_t sm = (size_t)(Px + lpb * (Px + 1)) * csz;
@@ -500,22 +566,25 @@ static int run_matvec(Handle* h, double omega, const double* d_omegas, int nb, c
             const double mu = 4e-7 * 3.14159265358979323846;
             T conv_scale = (T)(omega * mu * h->dx / ((double)Px * Py * Pz));
             dim3 grid((unsigned)((nlines + lpb - 1) / lpb));
-            k_xinv<T><<<grid, NTHR, sm, h->stream>>>(
+            k_xinv<T><<<grid, NTHR, sm, s>>>(
                 B1, x, y, Nvec, K, vidx, rows, nrows, nza, h->Kx, h->Ky,
                 static_cast<const int32_t*>(h->d_node.p), static_cast<const uint8_t*>(h->d_free.p),
                 static_cast<const double*>(h->d_lam.p), static_cast<const double*>(h->d_sig0.p), omega, mu,
                 h->dx, conv_scale, d_omegas, 1.0 / ((double)Px * Py * Pz), masked, px, twx, lpb, nlines);
         }
-        prof_mark(h, 5);
+        prof_at(h, 5, 1, s);
     }
-    // node rows
-    {
+    if (s_nd == s) {
+        prof_at(h, 6, 0, s);
         int64_t n = M * nb;
-        k_nodes<T><<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(
+        k_nodes<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
             x, y, Nvec, K, M, nb, static_cast<const int32_t*>(h->d_ninc.p),
             static_cast<const uint8_t*>(h->d_free.p), masked);
+        prof_at(h, 6, 1, s);
     }
-    prof_mark(h, 6);
+    // join: the caller's stream sees the second stream's work complete
+    SVH_CUDA_TRY(h, cudaStreamWaitEvent(s, h->ev_done, 0));
+    if (rc_aux) return rc_aux;
     if (h->prof_on && h->prof_calls < h->prof_max) ++h->prof_calls;
     SVH_CUDA_TRY(h, cudaGetLastError());
     return SVH_OK;
@@ -546,6 +615,7 @@ int launch_matvec_on(Handle* h, double omega, int nb, const void* x, void* y, in
 static int pass_variants(const Handle* h, int p, const PassArgs* pa = nullptr) {
     switch (p) {
         case 5: return pa && fused_path_ok(*pa, h->smem_optin) ? 2 : 1;
+        case 6: return 3;
         case 0: return x_fast_variants(h->Px, false, true);
         case 1: return y_fast_variants(h->Py, true);
         case 2: return z_fast_variants(h->Pz, true);
@@ -569,7 +639,7 @@ struct TuneKey {
     bool operator<(const TuneKey& o) const { return std::lexicographical_compare(v, v + 9, o.v, o.v + 9); }
 };
 static std::mutex g_tune_mu;
-static std::map<TuneKey, std::array<int, 6>> g_tune_cache;
+static std::map<TuneKey, std::array<int, SVH_NTUNE>> g_tune_cache;
 
 int autotune(Handle* h, int nb, int32_t* variants, double* ms) {
     const TuneKey key{{h->Px, h->Py, h->Pz, (int)h->zlist.size(), (int)h->rows.size(), h->Kx, h->Ky, h->Kz, nb}};
@@ -577,7 +647,7 @@ int autotune(Handle* h, int nb, int32_t* variants, double* ms) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end() && !ms) {
-            for (int p = 0; p < 6; ++p) {
+            for (int p = 0; p < SVH_NTUNE; ++p) {
                 h->tune32[p] = it->second[p];
                 if (variants) variants[p] = it->second[p];
             }
@@ -607,7 +677,7 @@ int autotune(Handle* h, int nb, int32_t* variants, double* ms) {
         return done(set_err(h, SVH_ERR_CUDA, "svh_autotune: CUDA set-up failed"));
     ensure_smem_optin(h);
     PassArgs pa = pass_args<float>(h, 2e9 * 3.14159265358979323846, nullptr, nb, x.p, y.p, 0, h->d_B1.p, h->d_B2.p);
-    std::array<int, 6> best{};
+    std::array<int, SVH_NTUNE> best{};
     constexpr int REPS = 5;
     for (int p = 0; p < 5; ++p) {
         const int nv = pass_variants(h, p);
@@ -661,6 +731,25 @@ int autotune(Handle* h, int nb, int32_t* variants, double* ms) {
     }
     h->tune32[5] = best[5];
     if (variants) variants[5] = best[5];
+    // 6: the stream schedule, timed on whole products (with the restore in rebuild mode)
+    {
+        float t[3] = {0, 0, 0};
+        for (int v = 0; v < 3; ++v) {
+            h->tune32[6] = v;
+            int rc = launch_matvec<float>(h, 2e9, nb, x.p, y.p, 0, nullptr);
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < REPS && !rc; ++r) rc = launch_matvec<float>(h, 2e9, nb, x.p, y.p, 0, nullptr);
+            cudaEventRecord(e1, s);
+            if (rc || cudaEventSynchronize(e1) != cudaSuccess) return done(rc ? rc : SVH_ERR_CUDA);
+            cudaEventElapsedTime(&t[v], e0, e1);
+        }
+        best[6] = 0;
+        for (int v = 1; v < 3; ++v)
+            if (t[v] < t[best[6]]) best[6] = v;
+        h->tune32[6] = best[6];
+        if (variants) variants[6] = best[6];
+        if (ms) ms[6] = t[best[6]] / REPS;
+    }
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_tune_cache[key] = best;
@@ -671,7 +760,7 @@ int autotune(Handle* h, int nb, int32_t* variants, double* ms) {
 int set_pass_variant(Handle* h, int pass, int variant) {
     ensure_smem_optin(h);
     const PassArgs pa = pass_args<float>(h, 1.0, nullptr, 1, nullptr, nullptr, 0, nullptr, nullptr);
-    if (pass < 0 || pass >= 6 || variant < 0 || variant >= std::max(1, pass_variants(h, pass, &pa)))
+    if (pass < 0 || pass >= SVH_NTUNE || variant < 0 || variant >= std::max(1, pass_variants(h, pass, &pa)))
         return set_err(h, SVH_ERR_ARG, "svh_set_pass_variant: no such pass or variant at this size");
     h->tune32[pass] = variant;
     return SVH_OK;
@@ -681,7 +770,7 @@ void get_pass_variants(const Handle* hc, int32_t* counts, int32_t* chosen) {
     Handle* h = const_cast<Handle*>(hc);   // reads the grid only (and caches a device attribute)
     ensure_smem_optin(h);
     const PassArgs pa = pass_args<float>(h, 1.0, nullptr, 1, nullptr, nullptr, 0, nullptr, nullptr);
-    for (int p = 0; p < 6; ++p) {
+    for (int p = 0; p < SVH_NTUNE; ++p) {
         if (counts) counts[p] = pass_variants(h, p, &pa);
         if (chosen) chosen[p] = h->tune32[p];
     }

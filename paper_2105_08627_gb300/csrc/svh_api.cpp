@@ -25,9 +25,9 @@ int cuda_err(Handle* h, cudaError_t e, const char* what) {
     return set_err(h, SVH_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-void prof_mark(Handle* h, int p) {
+void prof_at(Handle* h, int p, int end, cudaStream_t s) {
     if (!h->prof_on || h->prof_calls >= h->prof_max) return;
-    cudaEventRecord(h->prof_ev[(size_t)h->prof_calls * (SVH_NPASS + 1) + (p + 1)], h->stream);
+    cudaEventRecord(h->prof_ev[((size_t)h->prof_calls * SVH_NPASS + p) * 2 + end], s);
 }
 
 static void prof_release(Handle* h) {
@@ -501,6 +501,12 @@ int svh_destroy(svh_handle* hh) {
     if (!h) return SVH_ERR_ARG;
     cudaSetDevice(h->device);
     cudaStreamSynchronize(h->stream);
+    if (h->aux) {
+        cudaStreamSynchronize(h->aux);
+        cudaStreamDestroy(h->aux);
+    }
+    for (cudaEvent_t e : {h->ev_fork, h->ev_spec, h->ev_done, h->ev_x})
+        if (e) cudaEventDestroy(e);
     free_all(h);
     delete h;
     return SVH_OK;
@@ -783,7 +789,7 @@ int svh_rebuild_spectra(svh_handle* hh) {
     Handle* h = reinterpret_cast<Handle*>(hh);
     HCHECK(h);
     if (!h->have_kernels) return set_err(h, SVH_ERR_STATE, "svh_rebuild_spectra: no kernels");
-    return launch_tucker_rebuild(h);
+    return launch_tucker_rebuild(h, h->stream);
 }
 
 int svh_matvec(svh_handle* hh, double omega, int nb, const void* x, void* y, int precision) {
@@ -865,8 +871,12 @@ int svh_matvec_host(svh_handle* hh, double omega, int nb, const void* x, void* y
     int rc;
     if (h->d_xin.bytes < bytes && (rc = dev_alloc(h, h->d_xin, bytes))) return rc;
     if (h->d_yout.bytes < bytes && (rc = dev_alloc(h, h->d_yout, bytes))) return rc;
+    // fork the product's second stream first: the Tucker restore overlaps the input copy
+    if ((rc = matvec_prefork(h))) return rc;
     SVH_CUDA_TRY(h, cudaMemcpyAsync(h->d_xin.p, x, bytes, cudaMemcpyHostToDevice, h->stream));
+    if ((rc = matvec_mark_input_ready(h))) { h->preforked = false; return rc; }
     rc = svh_matvec(hh, omega, nb, h->d_xin.p, h->d_yout.p, precision);
+    h->preforked = false;   // consumed by the product (or left over by a rejected call)
     if (rc) return rc;
     SVH_CUDA_TRY(h, cudaMemcpyAsync(y, h->d_yout.p, bytes, cudaMemcpyDeviceToHost, h->stream));
     SVH_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
@@ -878,7 +888,7 @@ int svh_profile_begin(svh_handle* hh, int max_calls) {
     HCHECK(h);
     if (max_calls <= 0 || max_calls > 100000) return set_err(h, SVH_ERR_ARG, "svh_profile_begin: bad max_calls");
     prof_release(h);
-    h->prof_ev.resize((size_t)max_calls * (SVH_NPASS + 1));
+    h->prof_ev.resize((size_t)max_calls * SVH_NPASS * 2);
     for (auto& e : h->prof_ev) SVH_CUDA_TRY(h, cudaEventCreate(&e));
     h->prof_max = max_calls;
     h->prof_calls = 0;
@@ -891,12 +901,13 @@ int svh_profile_end(svh_handle* hh, double* ms, int* ncalls) {
     HCHECK(h);
     if (!h->prof_on || !ms || !ncalls) return set_err(h, SVH_ERR_STATE, "svh_profile_end: not profiling");
     SVH_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    if (h->aux) SVH_CUDA_TRY(h, cudaStreamSynchronize(h->aux));
     for (int p = 0; p < SVH_NPASS; ++p) ms[p] = 0.0;
     for (int c = 0; c < h->prof_calls; ++c)
         for (int p = 0; p < SVH_NPASS; ++p) {
             float t = 0.f;
-            SVH_CUDA_TRY(h, cudaEventElapsedTime(&t, h->prof_ev[(size_t)c * (SVH_NPASS + 1) + p],
-                                                 h->prof_ev[(size_t)c * (SVH_NPASS + 1) + p + 1]));
+            SVH_CUDA_TRY(h, cudaEventElapsedTime(&t, h->prof_ev[((size_t)c * SVH_NPASS + p) * 2],
+                                                 h->prof_ev[((size_t)c * SVH_NPASS + p) * 2 + 1]));
             ms[p] += t;
         }
     *ncalls = h->prof_calls;

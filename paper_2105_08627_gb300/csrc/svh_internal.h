@@ -75,7 +75,14 @@ struct Handle {
     // ---- per-pass profiling (svh_profile_begin/end)
     bool prof_on = false;
     int prof_max = 0, prof_calls = 0;
-    std::vector<cudaEvent_t> prof_ev;   // [prof_max][SVH_NPASS + 1]
+    std::vector<cudaEvent_t> prof_ev;   // [prof_max][SVH_NPASS][begin, end]
+    // second stream of the product: the Tucker restore and the node rows run on it,
+    // overlapping the x and y passes (joined by events before the z pass and at the end)
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_spec = nullptr, ev_done = nullptr, ev_x = nullptr;
+    // set by the host-buffer entry point: the second stream was forked before the input
+    // copy (the restore overlaps it) and ev_x marks the input on the device
+    bool preforked = false;
 
     // ---- sparse preconditioner (amg.cpp), built per frequency by the solver
     void* precond = nullptr;
@@ -91,13 +98,15 @@ struct Handle {
     DevBuf d_xin, d_yout;              // staging for svh_matvec_host
     DevBuf d_omegas;                   // per-item frequencies for svh_matvec_omegas
     DevBuf d_status;                   // int32 status word set by kernels (bounded waits that expired)
-    int tune32[6] = {0, 0, 0, 0, 0, 0};   // FP32 tile variant per FFT pass, [5]: 0 separate passes, 1 fused y/z/y
+    // FP32 tile variant per FFT pass; [5]: 0 separate passes, 1 fused y/z/y; [6] stream
+    // schedule: 0 restore + node rows on the second stream, 1 node rows only, 2 one stream
+    int tune32[7] = {0, 0, 0, 0, 0, 0, 0};
     size_t smem_optin = 0;                // opt-in shared memory per block of the device
 };
 
 int set_err(Handle* h, int code, const std::string& msg);
-// record the event that closes pass p (p = -1 opens a call) when profiling
-void prof_mark(Handle* h, int p);
+// record the begin (end = 0) or end (end = 1) event of pass p on stream s when profiling
+void prof_at(Handle* h, int p, int end, cudaStream_t s);
 int cuda_err(Handle* h, cudaError_t e, const char* what);
 int dev_alloc(Handle* h, DevBuf& b, size_t bytes);
 void dev_free(DevBuf& b);
@@ -112,10 +121,15 @@ int launch_matvec64(Handle* h, double omega, int nb, const void* x, void* y, int
 // same product on caller-provided intermediate grids (no allocation, no Tucker restore)
 int launch_matvec_on(Handle* h, double omega, int nb, const void* x, void* y, int precision, void* B1, void* B2);
 void matvec_scratch_bytes(const Handle* h, int nb, int precision, size_t* b1, size_t* b2);
+// fork the product's second stream now (before an input copy the caller enqueues next);
+// mark_input_ready records, after that copy, the event the node rows wait for
+int matvec_prefork(Handle* h);
+int matvec_mark_input_ready(Handle* h);
 // FFT tile variants (matvec.cu)
 int autotune(Handle* h, int nb, int32_t* variants, double* ms);
 int set_pass_variant(Handle* h, int pass, int variant);
 void get_pass_variants(const Handle* h, int32_t* counts, int32_t* chosen);
+#define SVH_NTUNE 7
 // quadrature of the unit kernels (kernels_gen.cu): fills T[7][Kz][Ky][Kx] (host)
 int generate_toeplitz_device(Handle* h, std::vector<double>& T);
 // sparse preconditioner (amg.cpp)
@@ -151,7 +165,7 @@ void amg_dev_destroy(void* d);
 int precond_schur_solve_dev(Handle* h, int nb, int per_freq, const void* e_dev, void* b_dev);
 // Tucker rebuild (tucker.cu)
 // restore the FP32 spectra from Tucker data (Eq. 10) into d_spec32
-int launch_tucker_rebuild(Handle* h);
+int launch_tucker_rebuild(Handle* h, cudaStream_t s);
 
 }  // namespace svh
 

@@ -213,7 +213,7 @@ static bool launch_mode3_h(const Mode3& m3, int nz, cudaStream_t st) {
     }
 }
 
-int launch_tucker_rebuild(Handle* h) {
+int launch_tucker_rebuild(Handle* h, cudaStream_t strm) {
     const int Hx = h->Hx, Hy = h->Hy, Hz = h->Hz;
     const int64_t Ht = (int64_t)Hx * Hy * Hz;
     size_t n1 = 0, n2 = 0;
@@ -261,8 +261,8 @@ int launch_tucker_rebuild(Handle* h) {
         }
         const size_t bytes = h->tk_probs.size();
         if (h->d_tk_probs.bytes < bytes) { int rc = dev_alloc(h, h->d_tk_probs, bytes); if (rc) return rc; }
-        SVH_CUDA_TRY(h, cudaMemcpyAsync(h->d_tk_probs.p, h->tk_probs.data(), bytes, cudaMemcpyHostToDevice, h->stream));
-        SVH_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+        SVH_CUDA_TRY(h, cudaMemcpyAsync(h->d_tk_probs.p, h->tk_probs.data(), bytes, cudaMemcpyHostToDevice, strm));
+        SVH_CUDA_TRY(h, cudaStreamSynchronize(strm));
         h->tk_probs_version = h->tk_version;
     }
     const GemmProb* all = reinterpret_cast<const GemmProb*>(h->tk_probs.data());
@@ -275,7 +275,7 @@ int launch_tucker_rebuild(Handle* h) {
             mt = std::max(mt, (all[off + i].M + GB_M - 1) / GB_M);
             nt = std::max(nt, (all[off + i].N + GB_N - 1) / GB_N);
         }
-        if (n) k_gemm_batched<<<dim3(nt, mt, n), 256, 0, h->stream>>>(dev + off);
+        if (n) k_gemm_batched<<<dim3(nt, mt, n), 256, 0, strm>>>(dev + off);
         off += n;
     }
     // mode 3
@@ -292,15 +292,15 @@ int launch_tucker_rebuild(Handle* h) {
         }
         m3.n = (int64_t)Hy * Hx;
         m3.Hz = Hz;
-        if (!launch_mode3_h(m3, nz, h->stream))
-            k_mode3<<<dim3((unsigned)((m3.n + 255) / 256), nz), 256, 0, h->stream>>>(m3);
+        if (!launch_mode3_h(m3, nz, strm))
+            k_mode3<<<dim3((unsigned)((m3.n + 255) / 256), nz), 256, 0, strm>>>(m3);
     } else if (nz) {
         int mt = 0, nt = 0;
         for (int i = 0; i < nz; ++i) {
             mt = std::max(mt, (all[off + i].M + GB_M - 1) / GB_M);
             nt = std::max(nt, (all[off + i].N + GB_N - 1) / GB_N);
         }
-        k_gemm_batched<<<dim3(nt, mt, nz), 256, 0, h->stream>>>(dev + off);
+        k_gemm_batched<<<dim3(nt, mt, nz), 256, 0, strm>>>(dev + off);
     }
     SVH_CUDA_TRY(h, cudaGetLastError());
     return SVH_OK;

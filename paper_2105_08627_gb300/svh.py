@@ -460,14 +460,15 @@ class Handle:
 
     PASSES = ("tucker_rebuild", "x_fwd", "y_fwd", "z_pass", "y_inv", "x_inv_epilogue", "node_rows")
 
-    FFT_PASSES = ("x_fwd", "y_fwd", "z_pass", "y_inv", "x_inv_epilogue", "path")
+    FFT_PASSES = ("x_fwd", "y_fwd", "z_pass", "y_inv", "x_inv_epilogue", "path", "streams")
 
     def autotune(self, nb):
         """Time every FP32 tile variant of the five FFT passes for nb items, then the
-        fused y/z/y path against the separate passes, and keep the fastest
-        -> (variants[6], ms per launch[6]); variants[5]: 0 separate passes, 1 fused."""
-        v = np.zeros(6, np.int32)
-        ms = np.zeros(6)
+        fused y/z/y path against the separate passes, then the stream schedules, and
+        keep the fastest -> (variants[7], ms per launch[7]); variants[5]: 0 separate passes,
+        1 fused; variants[6]: 0 restore + node rows overlapped, 1 node rows only, 2 one stream."""
+        v = np.zeros(7, np.int32)
+        ms = np.zeros(7)
         self._ck(lib().svh_autotune(self._h, int(nb), _i32p(v), _dp(ms)), "svh_autotune")
         return v, ms
 
@@ -482,9 +483,10 @@ class Handle:
 
     def pass_variants(self):
         """-> (number of variants per FFT pass (0: generic kernel), current choice);
-        entry 5 is the path (2 choices when the fused y/z/y kernel applies)."""
-        n = np.zeros(6, np.int32)
-        c = np.zeros(6, np.int32)
+        entry 5 is the path (2 choices when the fused y/z/y kernel applies), entry 6 the
+        stream schedule (3 choices)."""
+        n = np.zeros(7, np.int32)
+        c = np.zeros(7, np.int32)
         self._ck(lib().svh_get_pass_variants(self._h, _i32p(n), _i32p(c)), "svh_get_pass_variants")
         return n, c
 

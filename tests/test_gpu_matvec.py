@@ -177,10 +177,12 @@ def test_tucker_rebuild_matches_oracle_restore():
     yref = op.apply_K_fft(g, S7, x[0], om, P)[None]
     y = h.matvec(om, torch.from_numpy(x.astype(np.complex64)).cuda()).cpu().numpy().astype(np.complex128)
     _check_fp32(y, yref)
-    # rebuild-every-matvec mode gives the same result
+    # rebuild-every-matvec mode gives the same result, in every stream schedule
     h.set_kernel_mode(svh.SVH_KERNELS_TUCKER_REBUILD)
-    y2 = h.matvec(om, torch.from_numpy(x.astype(np.complex64)).cuda()).cpu().numpy().astype(np.complex128)
-    assert np.array_equal(y, y2)
+    for sched in (0, 1, 2):
+        h.set_pass_variant(6, sched)
+        y2 = h.matvec(om, torch.from_numpy(x.astype(np.complex64)).cuda()).cpu().numpy().astype(np.complex128)
+        assert np.array_equal(y, y2), sched
     h.close()
 
 
@@ -290,12 +292,16 @@ def test_every_tile_variant_and_autotune(seed, shape, fused):
             assert h.device_status() == 0          # no bounded wait (TMA z pass) expired
         h.set_pass_variant(p, 0)
     h.set_pass_variant(5, 0)
+    assert counts[6] == 3
+    for v in (1, 2, 0):                                                         # stream schedules
+        h.set_pass_variant(6, v)
+        _check_fp32(h.matvec(om, xd).cpu().numpy().astype(np.complex128), yref)
     with pytest.raises(Exception):
         h.set_pass_variant(0, counts[0])
     with pytest.raises(Exception):
         h.set_pass_variant(5, counts[5])
     v, ms = h.autotune(nb)
-    assert np.all((v >= 0) & (v < np.maximum(counts, 1))) and np.all(ms[:5] > 0)
+    assert np.all((v >= 0) & (v < np.maximum(counts, 1))) and np.all(ms[:5] > 0) and ms[6] > 0
     assert np.array_equal(h.pass_variants()[1], v)
     _check_fp32(h.matvec(om, xd).cpu().numpy().astype(np.complex128), yref)
     # FP64 products ignore the FP32 tile choices and the fused path
