@@ -47,12 +47,15 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="svh", choices=["svh", "reference"])
     p.add_argument("--nb", type=int, default=4, help="right-hand sides per step")
-    p.add_argument("--workload", default="meander256", choices=["meander256", "esfq512", "strip16"])
+    p.add_argument("--workload", default="meander256", choices=["meander256", "esfq512", "pair128", "strip16"])
     p.add_argument("--tucker-tol", type=float, default=1e-8)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-solve", action="store_true", help="skip the whole-solve timing block")
+    p.add_argument("--tiles", default=None,
+                   help="comma-separated FFT tile choices (7 values, as svh_autotune reports) "
+                        "instead of running the autotuner (e.g. for profiling)")
     p.add_argument("--with-tucker-sweep", action="store_true",
                    help="add CR / CO of the Tucker-compressed spectra vs tolerance on plates and cubes")
     p.add_argument("--with-batch", action="store_true",
@@ -66,6 +69,8 @@ def structure(name):
         return S.meander_cfg2(), "meander 256x256x8 over a holed ground plane (seed 202), 0.1 um voxels"
     if name == "esfq512":
         return S.esfq_cfg5(), "eSFQ-like 512x512x24 multilayer block (seed 505), 0.5 um voxels"
+    if name == "pair128":
+        return S.pair_cfg4(), "two overlapping meanders 128x128x16, log-normal lambda (seed 404), 0.1 um voxels"
     return S.strip_cfg1(), "strip 16x16x4 (1024 voxels), 0.1 um"
 
 
@@ -422,7 +427,12 @@ def run_svh(args):
     t_setup = time.perf_counter() - t_setup
     info = h.info()
     N, nb = info["N"], args.nb
-    tiles, tile_ms = h.autotune(nb)         # FFT tile variants, timed once before the run
+    if args.tiles:
+        tiles = np.array([int(v) for v in args.tiles.split(",")], np.int32)
+        for p_, v_ in enumerate(tiles):
+            h.set_pass_variant(p_, int(v_))
+    else:
+        tiles, tile_ms = h.autotune(nb)     # FFT tile variants, timed once before the run
     Kt = info["Kx"] * info["Ky"] * info["Kz"]
     omega = 2 * np.pi * s.freqs[0]
     x = torch.from_numpy(S.random_complex(1000 + rank, (nb, N)).astype(np.complex64)).cuda()
