@@ -530,7 +530,8 @@ def run_svh(args):
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(s)
-    launches_per_step = 2 + 6   # restore GEMMs (mode 3 fused into the z pass) + 6 passes
+    # restore (2 GEMMs + mode 3) + FFT passes (5 separate, or x / fused y-z-y / x) + node rows
+    launches_per_step = 3 + (3 if fused else 5) + 1
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
