@@ -372,7 +372,7 @@ def run_tucker_sweep(torch, svh, S):
     cases = [("plate", n, n, 4) for n in (128, 256, 512)] + [("cube", n, n, n) for n in (32, 64, 96)]
     stream = torch.cuda.current_stream().cuda_stream
     for kind, Kx, Ky, Kz in cases:
-        st = S.bar(Kx, Ky, Kz, 0, Kx, 0, Ky, 0, Kz, dx=1e-6)
+        st = S.bar(Kx, Ky, Kz, 0, Kx - 1, 0, Ky - 1, 0, Kz - 1, dx=1e-6)   # inclusive bounds: the full box
         h = svh.Handle(0, stream)
         h.setup_structure(st)
         h.generate_toeplitz()
