@@ -102,7 +102,10 @@ int svh_set_stream(svh_handle* h, void* stream);
  *                    cell (read only at non-empty cells; lambda > 0 there);
  *  ports[nports]   : terminal face lists (may be NULL when nports == 0).
  * Builds the voxel list, face nodes, the implicit incidence A, the port
- * terminals and gauge nodes, and picks FFT sizes. Errors: SVH_ERR_ARG for
+ * terminals and gauge nodes, and picks FFT sizes: per axis the smallest
+ * P >= 2K - 1 with size-specialised kernels (x, y: 16, 32, 48, 64, 96, 128,
+ * 192, 256, 384, 512, 768, 1024; z: 8, 12, 16, 24, 32, 48), else the
+ * smallest 2,3,5,7-smooth P >= 2K - 1 (2K first). Errors: SVH_ERR_ARG for
  * non-positive sizes or dx, an empty grid, lambda <= 0 on a voxel, or a port
  * face on an empty voxel. Invalidates previously loaded kernels. */
 int svh_setup_grid(svh_handle* h, int Kx, int Ky, int Kz, double dx,

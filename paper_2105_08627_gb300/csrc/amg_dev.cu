@@ -69,74 +69,87 @@ enum { S_D11 = 0, S_G1, S_A1, S_C1, S_C2, NSLOT };
 // top-level CG slots
 enum { F_BETA = 0, F_PQ, F_PQOLD, F_ALPHA, F_RR, F_BB, F_ACTIVE, F_ITERS, NFSLOT };
 
-// Block-wide sums of ND double2 values; the last block to finish (per
-// right-hand side, blockIdx.y) then sums all block partials in index order and
-// returns true with the totals in tot (valid in every thread of that block).
-template <int ND>
-__device__ bool block_sums_last(double2 (&val)[ND], double2* part, unsigned* cnt, double2 (&tot)[ND]) {
-    __shared__ double2 sh[TPB / 32][ND];
-    __shared__ bool last;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nblk = gridDim.x;
-    double2* pr = part + (int64_t)blockIdx.y * nblk * ND;
-#pragma unroll
-    for (int k = 0; k < ND; ++k) {
-        double x = val[k].x, y = val[k].y;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            x += __shfl_down_sync(0xffffffffu, x, o);
-            y += __shfl_down_sync(0xffffffffu, y, o);
+// ---- thread layout
+// Vectors are [row][rhs] (all right-hand sides of a row side by side). A
+// kernel over `rows` units (rows, or aggregates for the restriction) gives
+// each (unit, rhs) a group of G lanes: lane = (u * nrhs + rhs) * G + sub, with
+// U = TPB / (G nrhs) units per block pass and the blocks striding over the
+// unit blocks. A thread's rhs is fixed, so its dot-product terms accumulate in
+// registers; the lanes of a row's groups read the same matrix entries (one
+// transaction) and gather contiguous [rhs] values.
+struct Lanes {
+    int sub, rhs, uloc, U;
+    bool live;   // this lane belongs to a (unit, rhs) slot
+};
+
+__device__ __forceinline__ Lanes lanes(int G, int nrhs) {
+    Lanes l;
+    const int per = G * nrhs;
+    l.U = TPB / per;
+    l.live = (int)threadIdx.x < l.U * per;
+    l.sub = threadIdx.x % G;
+    l.rhs = (threadIdx.x / G) % nrhs;
+    l.uloc = threadIdx.x / per;
+    return l;
+}
+
+// In-place tree sum of the rows of red[rows][W] (shared) into red[0][*], in a
+// fixed order (deterministic); every thread of the block calls it.
+__device__ void reduce_rows(double2* red, int rows, int W) {
+    int st = 1;
+    while (st < rows) st <<= 1;
+    for (st >>= 1; st > 0; st >>= 1) {
+        __syncthreads();
+        for (int q = threadIdx.x; q < st * W; q += TPB) {
+            const int u = q / W, c = q - u * W;
+            if (u + st < rows) red[u * W + c] = add(red[u * W + c], red[(u + st) * W + c]);
         }
-        if (lane == 0) sh[warp][k] = d2(x, y);
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+}
+
+// Block sums of the ND per-thread values of each rhs (the leader lane, sub 0,
+// of every (unit, rhs) slot), then the last block to finish sums the block
+// partials; both sums are fixed-shape trees, so the results do not depend on
+// scheduling. Returns true in the last block with tot[rhs * ND + k] (shared)
+// filled; the other blocks return false.
+template <int ND>
+__device__ bool block_sums_last(const double2 (&val)[ND], int G, int nrhs, double2* part, unsigned* cnt,
+                                double2* tot) {
+    __shared__ double2 red[TPB * ND];
+    __shared__ bool last;
+    const int W = nrhs * ND, U = TPB / (G * nrhs);
+    const int sub = threadIdx.x % G, rhs = (threadIdx.x / G) % nrhs, uloc = threadIdx.x / (G * nrhs);
+    if (sub == 0 && uloc < U)
 #pragma unroll
-        for (int k = 0; k < ND; ++k) {
-            double2 s = sh[0][k];
-            for (int w = 1; w < TPB / 32; ++w) s = add(s, sh[w][k]);
-            pr[(int64_t)blockIdx.x * ND + k] = s;
-        }
-        __threadfence();
-        const unsigned t = atomicAdd(cnt + blockIdx.y, 1u);
-        last = (t == (unsigned)nblk - 1);
-    }
+        for (int k = 0; k < ND; ++k) red[uloc * W + rhs * ND + k] = val[k];
+    reduce_rows(red, U, W);
+    for (int q = threadIdx.x; q < W; q += TPB) part[(int64_t)blockIdx.x * W + q] = red[q];
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(cnt, 1u) == gridDim.x - 1;
     __syncthreads();
     if (!last) return false;
     __threadfence();
-    double2 acc[ND];
-#pragma unroll
-    for (int k = 0; k < ND; ++k) acc[k] = d2(0, 0);
-    for (int b = threadIdx.x; b < nblk; b += TPB)
-#pragma unroll
-        for (int k = 0; k < ND; ++k) acc[k] = add(acc[k], __ldcg(pr + (int64_t)b * ND + k));
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < ND; ++k) {
-        double x = acc[k].x, y = acc[k].y;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            x += __shfl_down_sync(0xffffffffu, x, o);
-            y += __shfl_down_sync(0xffffffffu, y, o);
-        }
-        if (lane == 0) sh[warp][k] = d2(x, y);
+    const int R = TPB / W;   // rows of partial sums, each over the blocks b = row (mod R)
+    if ((int)threadIdx.x < R * W) {
+        const int row = threadIdx.x / W, c = threadIdx.x - row * W;
+        double2 acc = d2(0, 0);
+        for (unsigned b = row; b < gridDim.x; b += R) acc = add(acc, __ldcg(part + (int64_t)b * W + c));
+        red[row * W + c] = acc;
     }
+    reduce_rows(red, R, W);
+    for (int q = threadIdx.x; q < W; q += TPB) tot[q] = red[q];
     __syncthreads();
-#pragma unroll
-    for (int k = 0; k < ND; ++k) {
-        double2 s = sh[0][k];
-        for (int w = 1; w < TPB / 32; ++w) s = add(s, sh[w][k]);
-        tot[k] = s;
-    }
-    if (threadIdx.x == 0) cnt[blockIdx.y] = 0;   // ready for the next launch
+    if (threadIdx.x == 0) *cnt = 0;   // ready for the next launch
     return true;
 }
 
-// Sparse rows are processed by groups of G lanes (G = 1 .. 32: one lane per
-// row on the large fine levels, more on the small coarse levels with long
-// Galerkin rows): lane `sub` of a group takes the row's entries
-// sub, sub + G, ...; the group's partial sums meet in one shuffle reduction
-// after the loops (every lane reaches it, so the shuffles stay convergent).
+// Sparse rows are taken by groups of G lanes (G = 1 .. 32: one lane per
+// (row, rhs) on the large fine levels, more on the small coarse levels with
+// long Galerkin rows): lane `sub` takes the row's entries sub, sub + G, ...;
+// the group's partial sums meet in one shuffle reduction after the loops
+// (every lane reaches it, so the shuffles stay convergent).
 template <int G>
 __device__ __forceinline__ double2 group_sum(double2 v) {
 #pragma unroll
@@ -147,80 +160,83 @@ __device__ __forceinline__ double2 group_sum(double2 v) {
     return v;   // complete in the group's lane 0
 }
 
-// K-cycle, first half: x0 = b / l1 (one l1-Jacobi sweep from zero), the
-// residual b - A x0 and its restriction to the aggregates (sum over each);
-// one group per aggregate.
-template <int G>
-__global__ void __launch_bounds__(TPB) k_kc_pre(int n, int nc, const int* __restrict__ rp, const int* __restrict__ ci,
-                                                const double* __restrict__ v, const double* __restrict__ l1inv,
-                                                const int* __restrict__ crp, const int* __restrict__ cidx, VRef B,
-                                                double2* __restrict__ rc) {
-    const int r = blockIdx.y;
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int c = (int)(t / G), sub = (int)(t % G);
-    const int64_t off = (int64_t)r * n;
-    const double2 cf = B.w ? B.coef[r] : d2(0, 0);
-    double2 s = d2(0, 0);
-    if (c < nc) {
-        for (int p = crp[c]; p < crp[c + 1]; ++p) {
-            const int i = cidx[p];
-            if (sub == 0) s = add(s, vget(B, off + i, cf));
-            for (int q = rp[i] + sub; q < rp[i + 1]; q += G) {
-                const int j = ci[q];
-                s = sub2(s, scl(v[q] * l1inv[j], vget(B, off + j, cf)));
-            }
-        }
-    }
-    s = group_sum<G>(s);
-    if (c < nc && sub == 0) rc[(int64_t)r * nc + c] = s;
+__device__ __forceinline__ double2 xcget(const XRef& X, int64_t idx, int r) {
+    if (!X.c1) return X.v1[idx];
+    return add(mul(X.c1[r], X.v1[idx]), mul(X.c2[r], X.v2[idx]));
 }
 
-__device__ __forceinline__ double2 xcget(const XRef& X, int64_t off, int r) {
-    if (!X.c1) return X.v1[off];
-    return add(mul(X.c1[r], X.v1[off]), mul(X.c2[r], X.v2[off]));
+// K-cycle, first half: x0 = b / l1 (one l1-Jacobi sweep from zero), the
+// residual b - A x0 and its restriction to the aggregates (sum over each);
+// one lane group per (aggregate, rhs).
+template <int G>
+__global__ void __launch_bounds__(TPB) k_kc_pre(int n, int nc, int nrhs, const int* __restrict__ rp,
+                                                const int* __restrict__ ci, const double* __restrict__ v,
+                                                const double* __restrict__ l1inv, const int* __restrict__ crp,
+                                                const int* __restrict__ cidx, VRef B, double2* __restrict__ rc) {
+    const Lanes L = lanes(G, nrhs);
+    const double2 cf = B.w ? B.coef[L.rhs] : d2(0, 0);
+    for (int64_t ub = blockIdx.x; ub * L.U < nc; ub += gridDim.x) {
+        const int64_t c = ub * L.U + L.uloc;
+        const bool act = L.live && c < nc;
+        double2 s = d2(0, 0);
+        if (act) {
+            for (int p = crp[c]; p < crp[c + 1]; ++p) {
+                const int i = cidx[p];
+                if (L.sub == 0) s = add(s, vget(B, (int64_t)i * nrhs + L.rhs, cf));
+                for (int q = rp[i] + L.sub; q < rp[i + 1]; q += G) {
+                    const int j = ci[q];
+                    s = sub2(s, scl(v[q] * l1inv[j], vget(B, (int64_t)j * nrhs + L.rhs, cf)));
+                }
+            }
+        }
+        s = group_sum<G>(s);
+        if (act && L.sub == 0) rc[c * nrhs + L.rhs] = s;
+    }
 }
 
 // K-cycle, second half: x1 = b / l1 + P xc (coarse correction), then one more
-// l1-Jacobi sweep x = x1 + (b - A x1) / l1; one group per row.
+// l1-Jacobi sweep x = x1 + (b - A x1) / l1; one lane group per (row, rhs).
 template <int G>
-__global__ void __launch_bounds__(TPB) k_kc_post(int n, int nc, const int* __restrict__ rp, const int* __restrict__ ci,
-                                                 const double* __restrict__ v, const double* __restrict__ l1inv,
-                                                 const int* __restrict__ agg, VRef B, XRef XC,
-                                                 double2* __restrict__ X) {
-    const int r = blockIdx.y;
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = (int)(t / G), sub = (int)(t % G);
-    const int64_t off = (int64_t)r * n, offc = (int64_t)r * nc;
-    const double2 cf = B.w ? B.coef[r] : d2(0, 0);
-    double2 ax = d2(0, 0);
-    if (i < n) {
-        for (int q = rp[i] + sub; q < rp[i + 1]; q += G) {
-            const int j = ci[q];
-            const double2 xj = add(scl(l1inv[j], vget(B, off + j, cf)), xcget(XC, offc + agg[j], r));
-            ax = add(ax, scl(v[q], xj));
+__global__ void __launch_bounds__(TPB) k_kc_post(int n, int nrhs, const int* __restrict__ rp,
+                                                 const int* __restrict__ ci, const double* __restrict__ v,
+                                                 const double* __restrict__ l1inv, const int* __restrict__ agg, VRef B,
+                                                 XRef XC, double2* __restrict__ X) {
+    const Lanes L = lanes(G, nrhs);
+    const double2 cf = B.w ? B.coef[L.rhs] : d2(0, 0);
+    for (int64_t ub = blockIdx.x; ub * L.U < n; ub += gridDim.x) {
+        const int64_t i = ub * L.U + L.uloc;
+        const bool act = L.live && i < n;
+        double2 ax = d2(0, 0);
+        if (act) {
+            for (int q = rp[i] + L.sub; q < rp[i + 1]; q += G) {
+                const int j = ci[q];
+                const int64_t jx = (int64_t)j * nrhs + L.rhs;
+                const double2 xj = add(scl(l1inv[j], vget(B, jx, cf)), xcget(XC, (int64_t)agg[j] * nrhs + L.rhs, L.rhs));
+                ax = add(ax, scl(v[q], xj));
+            }
         }
-    }
-    ax = group_sum<G>(ax);
-    if (i < n && sub == 0) {
-        const double2 bi = vget(B, off + i, cf);
-        const double2 xi = add(scl(l1inv[i], bi), xcget(XC, offc + agg[i], r));
-        X[off + i] = add(xi, scl(l1inv[i], sub2(bi, ax)));
+        ax = group_sum<G>(ax);
+        if (act && L.sub == 0) {
+            const int64_t ix = i * nrhs + L.rhs;
+            const double2 bi = vget(B, ix, cf);
+            const double2 xi = add(scl(l1inv[i], bi), xcget(XC, (int64_t)agg[i] * nrhs + L.rhs, L.rhs));
+            X[ix] = add(xi, scl(l1inv[i], sub2(bi, ax)));
+        }
     }
 }
 
-// coarsest level: X = C^{-1} b, one warp per row
-__global__ void k_dense(int n, const double* __restrict__ cinv, const double2* __restrict__ b,
+// coarsest level: X = C^{-1} b, one warp per (row, rhs)
+__global__ void k_dense(int n, int nrhs, const double* __restrict__ cinv, const double2* __restrict__ b,
                         double2* __restrict__ X) {
-    const int r = blockIdx.y;
-    const int row = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    const int64_t w = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
-    if (row >= n) return;
+    if (w >= (int64_t)n * nrhs) return;
+    const int row = (int)(w / nrhs), r = (int)(w % nrhs);
     const double* cr = cinv + (int64_t)row * n;
-    const double2* br = b + (int64_t)r * n;
     double x = 0, y = 0;
     for (int j = lane; j < n; j += 32) {
         const double c = cr[j];
-        const double2 bj = br[j];
+        const double2 bj = b[(int64_t)j * nrhs + r];
         x += c * bj.x;
         y += c * bj.y;
     }
@@ -229,192 +245,214 @@ __global__ void k_dense(int n, const double* __restrict__ cinv, const double2* _
         x += __shfl_down_sync(0xffffffffu, x, o);
         y += __shfl_down_sync(0xffffffffu, y, o);
     }
-    if (lane == 0) X[(int64_t)r * n + row] = d2(x, y);
+    if (lane == 0) X[(int64_t)row * nrhs + r] = d2(x, y);
 }
 
 // w = A vin with dot products; MODE 1 (first Krylov step): d11 = v1.w,
 // g1 = v1.b -> a1 = g1 / d11. MODE 2 (second): d12 = v1.w, d22 = v2.w,
 // g2 = v2.b -> (c1, c2) minimising the A-norm of the error over span{v1, v2}.
 template <int MODE, int G>
-__global__ void __launch_bounds__(TPB) k_kc_spmv(int n, const int* __restrict__ rp, const int* __restrict__ ci,
-                                                 const double* __restrict__ v, const double2* __restrict__ vin,
-                                                 const double2* __restrict__ v1, const double2* __restrict__ b,
-                                                 double2* __restrict__ w, double2* part, unsigned* cnt, double2* sc,
-                                                 int nrhs) {
-    const int r = blockIdx.y;
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = (int)(t / G), sub = (int)(t % G);
-    const int64_t off = (int64_t)r * n;
+__global__ void __launch_bounds__(TPB) k_kc_spmv(int n, int nrhs, const int* __restrict__ rp,
+                                                 const int* __restrict__ ci, const double* __restrict__ v,
+                                                 const double2* __restrict__ vin, const double2* __restrict__ v1,
+                                                 const double2* __restrict__ b, double2* __restrict__ w,
+                                                 double2* part, unsigned* cnt, double2* sc) {
     constexpr int ND = MODE == 1 ? 2 : 3;
+    __shared__ double2 tot[64 * ND];
+    const Lanes L = lanes(G, nrhs);
     double2 val[ND];
 #pragma unroll
     for (int k = 0; k < ND; ++k) val[k] = d2(0, 0);
-    double2 ax = d2(0, 0);
-    if (i < n)
-        for (int q = rp[i] + sub; q < rp[i + 1]; q += G) ax = add(ax, scl(v[q], vin[off + ci[q]]));
-    ax = group_sum<G>(ax);
-    if (i < n && sub == 0) {
-        w[off + i] = ax;
-        const double2 vi = vin[off + i], bi = b[off + i];
-        if (MODE == 1) {
-            val[0] = mul(vi, ax);
-            val[1] = mul(vi, bi);
-        } else {
-            val[0] = mul(v1[off + i], ax);
-            val[1] = mul(vi, ax);
-            val[2] = mul(vi, bi);
-        }
-    }
-    double2 tot[ND];
-    if (!block_sums_last<ND>(val, part, cnt, tot)) return;
-    if (threadIdx.x != 0) return;
-    double2* s = sc;
-    if (MODE == 1) {
-        const double2 d11 = tot[0], g1 = tot[1];
-        s[S_D11 * nrhs + r] = d11;
-        s[S_G1 * nrhs + r] = g1;
-        s[S_A1 * nrhs + r] = d2(d11.x > 0 ? g1.x / d11.x : 0.0, d11.y > 0 ? g1.y / d11.y : 0.0);
-    } else {
-        const double2 d11 = s[S_D11 * nrhs + r], g1 = s[S_G1 * nrhs + r], a1 = s[S_A1 * nrhs + r];
-        const double2 d12 = tot[0], d22 = tot[1], g2 = tot[2];
-        double c1[2], c2[2];
-        const double D11[2] = {d11.x, d11.y}, G1[2] = {g1.x, g1.y}, A1[2] = {a1.x, a1.y};
-        const double D12[2] = {d12.x, d12.y}, D22[2] = {d22.x, d22.y}, G2[2] = {g2.x, g2.y};
-        for (int k = 0; k < 2; ++k) {
-            const double det = D11[k] * D22[k] - D12[k] * D12[k];
-            if (det > 1e-14 * D11[k] * D22[k] && D11[k] > 0 && D22[k] > 0) {
-                c1[k] = (G1[k] * D22[k] - G2[k] * D12[k]) / det;
-                c2[k] = (D11[k] * G2[k] - D12[k] * G1[k]) / det;
+    for (int64_t ub = blockIdx.x; ub * L.U < n; ub += gridDim.x) {
+        const int64_t i = ub * L.U + L.uloc;
+        const bool act = L.live && i < n;
+        double2 ax = d2(0, 0);
+        if (act)
+            for (int q = rp[i] + L.sub; q < rp[i + 1]; q += G)
+                ax = add(ax, scl(v[q], vin[(int64_t)ci[q] * nrhs + L.rhs]));
+        ax = group_sum<G>(ax);
+        if (act && L.sub == 0) {
+            const int64_t ix = i * nrhs + L.rhs;
+            w[ix] = ax;
+            const double2 vi = vin[ix], bi = b[ix];
+            if (MODE == 1) {
+                val[0] = add(val[0], mul(vi, ax));
+                val[1] = add(val[1], mul(vi, bi));
             } else {
-                c1[k] = A1[k];
-                c2[k] = 0.0;
+                val[0] = add(val[0], mul(v1[ix], ax));
+                val[1] = add(val[1], mul(vi, ax));
+                val[2] = add(val[2], mul(vi, bi));
             }
         }
-        s[S_C1 * nrhs + r] = d2(c1[0], c1[1]);
-        s[S_C2 * nrhs + r] = d2(c2[0], c2[1]);
+    }
+    if (!block_sums_last<ND>(val, G, nrhs, part, cnt, tot)) return;
+    for (int r = threadIdx.x; r < nrhs; r += TPB) {
+        double2* s = sc;
+        if (MODE == 1) {
+            const double2 d11 = tot[r * ND], g1 = tot[r * ND + 1];
+            s[S_D11 * nrhs + r] = d11;
+            s[S_G1 * nrhs + r] = g1;
+            s[S_A1 * nrhs + r] = d2(d11.x > 0 ? g1.x / d11.x : 0.0, d11.y > 0 ? g1.y / d11.y : 0.0);
+        } else {
+            const double2 d11 = s[S_D11 * nrhs + r], g1 = s[S_G1 * nrhs + r], a1 = s[S_A1 * nrhs + r];
+            const double2 d12 = tot[r * ND], d22 = tot[r * ND + 1], g2 = tot[r * ND + 2];
+            double c1[2], c2[2];
+            const double D11[2] = {d11.x, d11.y}, G1[2] = {g1.x, g1.y}, A1[2] = {a1.x, a1.y};
+            const double D12[2] = {d12.x, d12.y}, D22[2] = {d22.x, d22.y}, G2[2] = {g2.x, g2.y};
+            for (int k = 0; k < 2; ++k) {
+                const double det = D11[k] * D22[k] - D12[k] * D12[k];
+                if (det > 1e-14 * D11[k] * D22[k] && D11[k] > 0 && D22[k] > 0) {
+                    c1[k] = (G1[k] * D22[k] - G2[k] * D12[k]) / det;
+                    c2[k] = (D11[k] * G2[k] - D12[k] * G1[k]) / det;
+                } else {
+                    c1[k] = A1[k];
+                    c2[k] = 0.0;
+                }
+            }
+            s[S_C1 * nrhs + r] = d2(c1[0], c1[1]);
+            s[S_C2 * nrhs + r] = d2(c2[0], c2[1]);
+        }
     }
 }
 
-// ---- top-level flexible CG on S
-// r = e, x = 0, bb = e.e; a system with bb = 0 starts (and stays) inactive
-__global__ void __launch_bounds__(TPB) k_fcg_init(int n, const double2* __restrict__ e, double2* __restrict__ x,
-                                                  double2* __restrict__ rr, double2* part, unsigned* cnt, double2* fs,
-                                                  int nrhs) {
-    const int r = blockIdx.y;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t off = (int64_t)r * n;
+// ---- top-level flexible CG on S (one lane per (row, rhs))
+// r = e (e given as [rhs][n]), x = 0, bb = e.e; a system with bb = 0 starts (and stays) inactive
+__global__ void __launch_bounds__(TPB) k_fcg_init(int n, int nrhs, const double2* __restrict__ e,
+                                                  double2* __restrict__ x, double2* __restrict__ rr, double2* part,
+                                                  unsigned* cnt, double2* fs) {
+    __shared__ double2 tot[64];
+    const Lanes L = lanes(1, nrhs);
     double2 val[1] = {d2(0, 0)};
-    if (i < n) {
-        const double2 ei = e[off + i];
-        rr[off + i] = ei;
-        x[off + i] = d2(0, 0);
-        val[0] = mul(ei, ei);
+    for (int64_t ub = blockIdx.x; ub * L.U < n; ub += gridDim.x) {
+        const int64_t i = ub * L.U + L.uloc;
+        if (L.live && i < n) {
+            const double2 ei = e[(int64_t)L.rhs * n + i];
+            rr[i * nrhs + L.rhs] = ei;
+            x[i * nrhs + L.rhs] = d2(0, 0);
+            val[0] = add(val[0], mul(ei, ei));
+        }
     }
-    double2 tot[1];
-    if (!block_sums_last<1>(val, part, cnt, tot)) return;
-    if (threadIdx.x != 0) return;
-    fs[F_BB * nrhs + r] = tot[0];
-    fs[F_RR * nrhs + r] = tot[0];
-    fs[F_ACTIVE * nrhs + r] = d2(tot[0].x > 0 ? 1.0 : 0.0, tot[0].y > 0 ? 1.0 : 0.0);
-    fs[F_ITERS * nrhs + r] = d2(0, 0);
-    fs[F_BETA * nrhs + r] = d2(0, 0);
-    fs[F_PQOLD * nrhs + r] = d2(0, 0);
+    if (!block_sums_last<1>(val, 1, nrhs, part, cnt, tot)) return;
+    for (int r = threadIdx.x; r < nrhs; r += TPB) {
+        fs[F_BB * nrhs + r] = tot[r];
+        fs[F_RR * nrhs + r] = tot[r];
+        fs[F_ACTIVE * nrhs + r] = d2(tot[r].x > 0 ? 1.0 : 0.0, tot[r].y > 0 ? 1.0 : 0.0);
+        fs[F_ITERS * nrhs + r] = d2(0, 0);
+        fs[F_BETA * nrhs + r] = d2(0, 0);
+        fs[F_PQOLD * nrhs + r] = d2(0, 0);
+    }
 }
 
 // beta = (z . q_old) / (p_old . q_old): the new direction is S-orthogonal to the previous one
-__global__ void __launch_bounds__(TPB) k_fcg_beta(int n, const double2* __restrict__ z,
+__global__ void __launch_bounds__(TPB) k_fcg_beta(int n, int nrhs, const double2* __restrict__ z,
                                                   const double2* __restrict__ qold, double2* part, unsigned* cnt,
-                                                  double2* fs, int nrhs) {
-    const int r = blockIdx.y;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t off = (int64_t)r * n;
+                                                  double2* fs) {
+    __shared__ double2 tot[64];
+    const Lanes L = lanes(1, nrhs);
     double2 val[1] = {d2(0, 0)};
-    if (i < n) val[0] = mul(z[off + i], qold[off + i]);
-    double2 tot[1];
-    if (!block_sums_last<1>(val, part, cnt, tot)) return;
-    if (threadIdx.x != 0) return;
-    const double2 pq = fs[F_PQOLD * nrhs + r];
-    fs[F_BETA * nrhs + r] = d2(pq.x > 0 ? tot[0].x / pq.x : 0.0, pq.y > 0 ? tot[0].y / pq.y : 0.0);
+    for (int64_t ub = blockIdx.x; ub * L.U < n; ub += gridDim.x) {
+        const int64_t i = ub * L.U + L.uloc;
+        if (L.live && i < n) val[0] = add(val[0], mul(z[i * nrhs + L.rhs], qold[i * nrhs + L.rhs]));
+    }
+    if (!block_sums_last<1>(val, 1, nrhs, part, cnt, tot)) return;
+    for (int r = threadIdx.x; r < nrhs; r += TPB) {
+        const double2 pq = fs[F_PQOLD * nrhs + r];
+        fs[F_BETA * nrhs + r] = d2(pq.x > 0 ? tot[r].x / pq.x : 0.0, pq.y > 0 ? tot[r].y / pq.y : 0.0);
+    }
 }
 
 // p = z - beta p_old (p = z on the first iteration)
-__global__ void k_fcg_dir(int64_t n, const double2* __restrict__ z, const double2* __restrict__ pold,
-                          double2* __restrict__ p, const double2* __restrict__ fs, int nrhs, int first) {
-    const int r = blockIdx.y;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int64_t o = r * n + i;
-    p[o] = first ? z[o] : sub2(z[o], mul(fs[F_BETA * nrhs + r], pold[o]));
+__global__ void k_fcg_dir(int64_t total, int nrhs, const double2* __restrict__ z, const double2* __restrict__ pold,
+                          double2* __restrict__ p, const double2* __restrict__ fs, int first) {
+    const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= total) return;
+    p[o] = first ? z[o] : sub2(z[o], mul(fs[F_BETA * nrhs + (int)(o % nrhs)], pold[o]));
 }
 
 // q = S p, pq = p.q, alpha = (p.r) / pq for the active systems (0 for the others)
 template <int G>
-__global__ void __launch_bounds__(TPB) k_fcg_spmv(int n, const int* __restrict__ rp, const int* __restrict__ ci,
-                                                  const double* __restrict__ v, const double2* __restrict__ p,
-                                                  const double2* __restrict__ rr, double2* __restrict__ q,
-                                                  double2* part, unsigned* cnt, double2* fs, int nrhs) {
-    const int r = blockIdx.y;
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = (int)(t / G), sub = (int)(t % G);
-    const int64_t off = (int64_t)r * n;
+__global__ void __launch_bounds__(TPB) k_fcg_spmv(int n, int nrhs, const int* __restrict__ rp,
+                                                  const int* __restrict__ ci, const double* __restrict__ v,
+                                                  const double2* __restrict__ p, const double2* __restrict__ rr,
+                                                  double2* __restrict__ q, double2* part, unsigned* cnt, double2* fs) {
+    __shared__ double2 tot[64 * 2];
+    const Lanes L = lanes(G, nrhs);
     double2 val[2] = {d2(0, 0), d2(0, 0)};
-    double2 ax = d2(0, 0);
-    if (i < n)
-        for (int k = rp[i] + sub; k < rp[i + 1]; k += G) ax = add(ax, scl(v[k], p[off + ci[k]]));
-    ax = group_sum<G>(ax);
-    if (i < n && sub == 0) {
-        q[off + i] = ax;
-        const double2 pi = p[off + i];
-        val[0] = mul(pi, ax);
-        val[1] = mul(pi, rr[off + i]);
+    for (int64_t ub = blockIdx.x; ub * L.U < n; ub += gridDim.x) {
+        const int64_t i = ub * L.U + L.uloc;
+        const bool act = L.live && i < n;
+        double2 ax = d2(0, 0);
+        if (act)
+            for (int k = rp[i] + L.sub; k < rp[i + 1]; k += G) ax = add(ax, scl(v[k], p[(int64_t)ci[k] * nrhs + L.rhs]));
+        ax = group_sum<G>(ax);
+        if (act && L.sub == 0) {
+            const int64_t ix = i * nrhs + L.rhs;
+            q[ix] = ax;
+            const double2 pi = p[ix];
+            val[0] = add(val[0], mul(pi, ax));
+            val[1] = add(val[1], mul(pi, rr[ix]));
+        }
     }
-    double2 tot[2];
-    if (!block_sums_last<2>(val, part, cnt, tot)) return;
-    if (threadIdx.x != 0) return;
-    const double2 act = fs[F_ACTIVE * nrhs + r];
-    const double2 pq = tot[0], pr = tot[1];
-    fs[F_PQ * nrhs + r] = pq;
-    fs[F_ALPHA * nrhs + r] = d2(act.x > 0 && pq.x > 0 ? pr.x / pq.x : 0.0, act.y > 0 && pq.y > 0 ? pr.y / pq.y : 0.0);
+    if (!block_sums_last<2>(val, G, nrhs, part, cnt, tot)) return;
+    for (int r = threadIdx.x; r < nrhs; r += TPB) {
+        const double2 act = fs[F_ACTIVE * nrhs + r];
+        const double2 pq = tot[r * 2], pr = tot[r * 2 + 1];
+        fs[F_PQ * nrhs + r] = pq;
+        fs[F_ALPHA * nrhs + r] =
+            d2(act.x > 0 && pq.x > 0 ? pr.x / pq.x : 0.0, act.y > 0 && pq.y > 0 ? pr.y / pq.y : 0.0);
+    }
 }
 
 // x += alpha p, r -= alpha q; rr = r.r; a system stays active while ||r|| > tol ||e||
-__global__ void __launch_bounds__(TPB) k_fcg_update(int n, const double2* __restrict__ p,
+__global__ void __launch_bounds__(TPB) k_fcg_update(int n, int nrhs, const double2* __restrict__ p,
                                                     const double2* __restrict__ q, double2* __restrict__ x,
                                                     double2* __restrict__ rr, double2* part, unsigned* cnt,
-                                                    double2* fs, int nrhs, double tol2) {
-    const int r = blockIdx.y;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t off = (int64_t)r * n;
-    const double2 alpha = fs[F_ALPHA * nrhs + r];
+                                                    double2* fs, double tol2) {
+    __shared__ double2 tot[64];
+    const Lanes L = lanes(1, nrhs);
+    const double2 alpha = fs[F_ALPHA * nrhs + L.rhs];
     double2 val[1] = {d2(0, 0)};
-    if (i < n) {
-        const double2 xi = add(x[off + i], mul(alpha, p[off + i]));
-        const double2 ri = sub2(rr[off + i], mul(alpha, q[off + i]));
-        x[off + i] = xi;
-        rr[off + i] = ri;
-        val[0] = mul(ri, ri);
+    for (int64_t ub = blockIdx.x; ub * L.U < n; ub += gridDim.x) {
+        const int64_t i = ub * L.U + L.uloc;
+        if (L.live && i < n) {
+            const int64_t ix = i * nrhs + L.rhs;
+            const double2 xi = add(x[ix], mul(alpha, p[ix]));
+            const double2 ri = sub2(rr[ix], mul(alpha, q[ix]));
+            x[ix] = xi;
+            rr[ix] = ri;
+            val[0] = add(val[0], mul(ri, ri));
+        }
     }
-    double2 tot[1];
-    if (!block_sums_last<1>(val, part, cnt, tot)) return;
-    if (threadIdx.x != 0) return;
-    const double2 bb = fs[F_BB * nrhs + r], act = fs[F_ACTIVE * nrhs + r];
-    double2 it = fs[F_ITERS * nrhs + r];
-    it.x += act.x;
-    it.y += act.y;
-    fs[F_ITERS * nrhs + r] = it;
-    fs[F_RR * nrhs + r] = tot[0];
-    fs[F_ACTIVE * nrhs + r] = d2(act.x > 0 && tot[0].x > tol2 * bb.x ? 1.0 : 0.0,
-                                 act.y > 0 && tot[0].y > tol2 * bb.y ? 1.0 : 0.0);
-    fs[F_PQOLD * nrhs + r] = fs[F_PQ * nrhs + r];
+    if (!block_sums_last<1>(val, 1, nrhs, part, cnt, tot)) return;
+    for (int r = threadIdx.x; r < nrhs; r += TPB) {
+        const double2 bb = fs[F_BB * nrhs + r], act = fs[F_ACTIVE * nrhs + r];
+        double2 it = fs[F_ITERS * nrhs + r];
+        it.x += act.x;
+        it.y += act.y;
+        fs[F_ITERS * nrhs + r] = it;
+        fs[F_RR * nrhs + r] = tot[r];
+        fs[F_ACTIVE * nrhs + r] = d2(act.x > 0 && tot[r].x > tol2 * bb.x ? 1.0 : 0.0,
+                                     act.y > 0 && tot[r].y > tol2 * bb.y ? 1.0 : 0.0);
+        fs[F_PQOLD * nrhs + r] = fs[F_PQ * nrhs + r];
+    }
+}
+
+// solution out in the caller's [rhs][n] layout
+__global__ void k_fcg_out(int n, int nrhs, const double2* __restrict__ x, double2* __restrict__ b) {
+    const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= (int64_t)n * nrhs) return;
+    const int64_t i = o / nrhs;
+    const int r = (int)(o % nrhs);
+    b[(int64_t)r * n + i] = x[o];
 }
 
 // ---- device copy of one hierarchy
 struct DLevel {
     int n = 0, nc = 0;
-    int g = 1, gp = 1;           // lanes per row (SpMV kernels) and per aggregate (restriction)
+    double per_row = 1, per_agg = 1;   // mean entries per row, and per aggregate (restriction)
     bool krylov = true;          // coarse solves on this level take the two Krylov steps
     DevBuf rp, ci, v, l1inv, agg, crp, cidx;
-    DevBuf v1, w1, v2, w2, rc;   // [nrhs][n] (rc: [nrhs][nc])
+    DevBuf v1, w1, v2, w2, rc;   // [n][nrhs] (rc: [nc][nrhs])
     DevBuf sc, part, cnt;        // scalar slots, block partials, completion counters
 };
 
@@ -448,13 +486,23 @@ struct DevAmg {
 
 unsigned nblk(int64_t n) { return (unsigned)((n + TPB - 1) / TPB); }
 
-// lanes per unit (row or aggregate) for `units` units of `per` entries on average:
-// one lane per unit while the units alone fill the GPU (~160 K threads), more on
-// the small coarse levels (whose Galerkin rows are long), at most one per entry
-int lanes_for(int64_t units, double per) {
+constexpr int kMaxGrid = 152 * 8;   // blocks of a grid-striding kernel (and block partials)
+constexpr int kMaxRhs = 64;         // right-hand sides per solve (complex; 2 real systems each)
+
+// launch shape of a kernel over `units` units of `per` entries for nrhs right-hand sides:
+// G lanes per (unit, rhs) -- one while the (unit, rhs) slots alone fill the GPU
+// (~160 K threads), more on the small coarse levels (long Galerkin rows), at most one
+// per entry and G nrhs <= TPB -- and the grid (capped: the blocks stride)
+struct Geo {
+    int G;
+    unsigned grid;
+};
+Geo geo(int64_t units, double per, int nrhs) {
     int g = 1;
-    while (g < 32 && g < per && (int64_t)g * units < 160000) g *= 2;
-    return g;
+    while (g < 32 && g < per && (int64_t)g * units * nrhs < 160000 && 2 * g * nrhs <= TPB) g *= 2;
+    const int U = TPB / (g * nrhs);
+    const int64_t blocks = (units + U - 1) / U;
+    return {g, (unsigned)std::max<int64_t>(1, std::min<int64_t>(blocks, kMaxGrid))};
 }
 
 template <typename T>
@@ -472,11 +520,11 @@ int upload(Handle* h, DevAmg& D, const AmgView& A) {
         L.n = V.n;
         L.nc = l + 1 < nl ? V.nc : 0;
         const int nnz = V.rp[V.n];
-        L.g = lanes_for(V.n, (double)nnz / std::max(1, V.n));
+        L.per_row = (double)nnz / std::max(1, V.n);
         // the K-cycle's two Krylov steps double the visits of every level below; on the
         // small levels (latency-bound launches) one cycle is cheaper overall
         L.krylov = V.n >= kKrylovMinRows;
-        L.gp = L.nc > 0 ? lanes_for(L.nc, (double)nnz / L.nc) : 1;
+        L.per_agg = L.nc > 0 ? (double)nnz / L.nc : 1;
         std::vector<double> inv(V.n);
         for (int i = 0; i < V.n; ++i) inv[i] = 1.0 / V.l1[i];
         int rc;
@@ -521,20 +569,18 @@ int ensure_work(Handle* h, DevAmg& D, int nrhs) {
         if ((rc = dev_alloc(h, L.v1, vb)) || (rc = dev_alloc(h, L.w1, vb)) || (rc = dev_alloc(h, L.v2, vb)) ||
             (rc = dev_alloc(h, L.w2, vb)) || (rc = dev_alloc(h, L.rc, (size_t)nrhs * (L.nc > 0 ? L.nc : 1) * 16)) ||
             (rc = dev_alloc(h, L.sc, (size_t)NSLOT * nrhs * 16)) ||
-            (rc = dev_alloc(h, L.part, (size_t)nrhs * nblk((int64_t)L.n * L.g) * 3 * 16)) ||
-            (rc = dev_alloc(h, L.cnt, (size_t)nrhs * 4)))
+            (rc = dev_alloc(h, L.part, (size_t)nrhs * kMaxGrid * 3 * 16)) || (rc = dev_alloc(h, L.cnt, 4)))
             return rc;
-        SVH_CUDA_TRY(h, cudaMemsetAsync(L.cnt.p, 0, (size_t)nrhs * 4, D.st));
+        SVH_CUDA_TRY(h, cudaMemsetAsync(L.cnt.p, 0, 4, D.st));
         SVH_CUDA_TRY(h, cudaMemsetAsync(L.sc.p, 0, (size_t)NSLOT * nrhs * 16, D.st));
     }
     const size_t vb = (size_t)nrhs * D.lv[0].n * 16;
     if ((rc = dev_alloc(h, D.fx, vb)) || (rc = dev_alloc(h, D.fr, vb)) || (rc = dev_alloc(h, D.fz, vb)) ||
         (rc = dev_alloc(h, D.fp, vb)) || (rc = dev_alloc(h, D.fq, vb)) || (rc = dev_alloc(h, D.fpo, vb)) ||
         (rc = dev_alloc(h, D.fqo, vb)) || (rc = dev_alloc(h, D.fs, (size_t)NFSLOT * nrhs * 16)) ||
-        (rc = dev_alloc(h, D.fpart, (size_t)nrhs * std::max(nblk((int64_t)D.lv[0].n * D.lv[0].g), nblk(D.lv[0].n)) * 2 * 16)) ||
-        (rc = dev_alloc(h, D.fcnt, (size_t)nrhs * 4)))
+        (rc = dev_alloc(h, D.fpart, (size_t)nrhs * kMaxGrid * 2 * 16)) || (rc = dev_alloc(h, D.fcnt, 4)))
         return rc;
-    SVH_CUDA_TRY(h, cudaMemsetAsync(D.fcnt.p, 0, (size_t)nrhs * 4, D.st));
+    SVH_CUDA_TRY(h, cudaMemsetAsync(D.fcnt.p, 0, 4, D.st));
     if (D.host_fs) cudaFreeHost(D.host_fs);
     D.host_fs = nullptr;
     SVH_CUDA_TRY(h, cudaMallocHost(&D.host_fs, (size_t)NFSLOT * nrhs * 16));
@@ -545,46 +591,49 @@ int ensure_work(Handle* h, DevAmg& D, int nrhs) {
 void kcycle(Handle* h, DevAmg& D, int l, VRef B, double2* X, int nrhs);
 
 template <int G>
-void launch_pre(DLevel& L, VRef B, int nrhs, cudaStream_t s) {
-    k_kc_pre<G><<<dim3(nblk((int64_t)L.nc * G), nrhs), TPB, 0, s>>>(L.n, L.nc, P<int>(L.rp), P<int>(L.ci),
-                                                                   P<double>(L.v), P<double>(L.l1inv), P<int>(L.crp),
-                                                                   P<int>(L.cidx), B, P<double2>(L.rc));
+void launch_pre(DLevel& L, VRef B, int nrhs, unsigned grid, cudaStream_t s) {
+    k_kc_pre<G><<<grid, TPB, 0, s>>>(L.n, L.nc, nrhs, P<int>(L.rp), P<int>(L.ci), P<double>(L.v), P<double>(L.l1inv),
+                                     P<int>(L.crp), P<int>(L.cidx), B, P<double2>(L.rc));
 }
 
 template <int G>
-void launch_post(DLevel& L, VRef B, XRef XC, double2* X, int nrhs, cudaStream_t s) {
-    k_kc_post<G><<<dim3(nblk((int64_t)L.n * G), nrhs), TPB, 0, s>>>(L.n, L.nc, P<int>(L.rp), P<int>(L.ci),
-                                                                    P<double>(L.v), P<double>(L.l1inv), P<int>(L.agg),
-                                                                    B, XC, X);
+void launch_post(DLevel& L, VRef B, XRef XC, double2* X, int nrhs, unsigned grid, cudaStream_t s) {
+    k_kc_post<G><<<grid, TPB, 0, s>>>(L.n, nrhs, P<int>(L.rp), P<int>(L.ci), P<double>(L.v), P<double>(L.l1inv),
+                                      P<int>(L.agg), B, XC, X);
 }
 
 template <int MODE, int G>
 void launch_spmv_kc(DLevel& L, const double2* vin, const double2* v1, const double2* b, double2* w, int nrhs,
-                    cudaStream_t s) {
-    k_kc_spmv<MODE, G><<<dim3(nblk((int64_t)L.n * G), nrhs), TPB, 0, s>>>(
-        L.n, P<int>(L.rp), P<int>(L.ci), P<double>(L.v), vin, v1, b, w, P<double2>(L.part), P<unsigned>(L.cnt),
-        P<double2>(L.sc), nrhs);
+                    unsigned grid, cudaStream_t s) {
+    k_kc_spmv<MODE, G><<<grid, TPB, 0, s>>>(L.n, nrhs, P<int>(L.rp), P<int>(L.ci), P<double>(L.v), vin, v1, b, w,
+                                            P<double2>(L.part), P<unsigned>(L.cnt), P<double2>(L.sc));
 }
 
 template <int MODE>
 void spmv_kc(DLevel& L, const double2* vin, const double2* v1, const double2* b, double2* w, int nrhs,
              cudaStream_t s) {
-    switch (L.g) {
-        case 1: launch_spmv_kc<MODE, 1>(L, vin, v1, b, w, nrhs, s); break;
-        case 2: launch_spmv_kc<MODE, 2>(L, vin, v1, b, w, nrhs, s); break;
-        case 4: launch_spmv_kc<MODE, 4>(L, vin, v1, b, w, nrhs, s); break;
-        case 8: launch_spmv_kc<MODE, 8>(L, vin, v1, b, w, nrhs, s); break;
-        case 16: launch_spmv_kc<MODE, 16>(L, vin, v1, b, w, nrhs, s); break;
-        default: launch_spmv_kc<MODE, 32>(L, vin, v1, b, w, nrhs, s); break;
+    const Geo q = geo(L.n, L.per_row, nrhs);
+    switch (q.G) {
+        case 1: launch_spmv_kc<MODE, 1>(L, vin, v1, b, w, nrhs, q.grid, s); break;
+        case 2: launch_spmv_kc<MODE, 2>(L, vin, v1, b, w, nrhs, q.grid, s); break;
+        case 4: launch_spmv_kc<MODE, 4>(L, vin, v1, b, w, nrhs, q.grid, s); break;
+        case 8: launch_spmv_kc<MODE, 8>(L, vin, v1, b, w, nrhs, q.grid, s); break;
+        case 16: launch_spmv_kc<MODE, 16>(L, vin, v1, b, w, nrhs, q.grid, s); break;
+        default: launch_spmv_kc<MODE, 32>(L, vin, v1, b, w, nrhs, q.grid, s); break;
     }
 }
 
 template <int G>
-void launch_fcg_spmv(DLevel& L0, const double2* p, const double2* r, double2* q, DevAmg& D, int nrhs,
+void launch_fcg_spmv(DLevel& L0, const double2* p, const double2* r, double2* q, DevAmg& D, int nrhs, unsigned grid,
                      cudaStream_t s) {
-    k_fcg_spmv<G><<<dim3(nblk((int64_t)L0.n * G), nrhs), TPB, 0, s>>>(L0.n, P<int>(L0.rp), P<int>(L0.ci),
-                                                                      P<double>(L0.v), p, r, q, P<double2>(D.fpart),
-                                                                      P<unsigned>(D.fcnt), P<double2>(D.fs), nrhs);
+    k_fcg_spmv<G><<<grid, TPB, 0, s>>>(L0.n, nrhs, P<int>(L0.rp), P<int>(L0.ci), P<double>(L0.v), p, r, q,
+                                       P<double2>(D.fpart), P<unsigned>(D.fcnt), P<double2>(D.fs));
+}
+
+void dense(DevAmg& D, const double2* b, double2* X, int nrhs, cudaStream_t s) {
+    const int n = D.lv.back().n;
+    const int64_t warps = (int64_t)n * nrhs;
+    k_dense<<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(n, nrhs, P<double>(D.cinv), b, X);
 }
 
 // two Krylov steps on level l with the level-l cycle as preconditioner; the
@@ -594,7 +643,7 @@ void coarse_krylov(Handle* h, DevAmg& D, int l, const double2* b, int nrhs) {
     DLevel& L = D.lv[l];
     cudaStream_t s = D.st;
     if (l + 1 == (int)D.lv.size()) {
-        k_dense<<<dim3((L.n + 7) / 8, nrhs), 256, 0, s>>>(L.n, P<double>(D.cinv), b, P<double2>(L.v1));
+        dense(D, b, P<double2>(L.v1), nrhs, s);
         return;
     }
     if (!L.krylov) {   // small level: one cycle, no Krylov acceleration (result in v1)
@@ -612,13 +661,14 @@ void kcycle(Handle* h, DevAmg& D, int l, VRef B, double2* X, int nrhs) {
     DLevel& L = D.lv[l];
     DLevel& C = D.lv[l + 1];
     cudaStream_t s = D.st;
-    switch (L.gp) {
-        case 1: launch_pre<1>(L, B, nrhs, s); break;
-        case 2: launch_pre<2>(L, B, nrhs, s); break;
-        case 4: launch_pre<4>(L, B, nrhs, s); break;
-        case 8: launch_pre<8>(L, B, nrhs, s); break;
-        case 16: launch_pre<16>(L, B, nrhs, s); break;
-        default: launch_pre<32>(L, B, nrhs, s); break;
+    const Geo qa = geo(L.nc, L.per_agg, nrhs);
+    switch (qa.G) {
+        case 1: launch_pre<1>(L, B, nrhs, qa.grid, s); break;
+        case 2: launch_pre<2>(L, B, nrhs, qa.grid, s); break;
+        case 4: launch_pre<4>(L, B, nrhs, qa.grid, s); break;
+        case 8: launch_pre<8>(L, B, nrhs, qa.grid, s); break;
+        case 16: launch_pre<16>(L, B, nrhs, qa.grid, s); break;
+        default: launch_pre<32>(L, B, nrhs, qa.grid, s); break;
     }
     coarse_krylov(h, D, l + 1, P<double2>(L.rc), nrhs);
     XRef XC{P<double2>(C.v1), P<double2>(C.v2), nullptr, nullptr};
@@ -626,13 +676,14 @@ void kcycle(Handle* h, DevAmg& D, int l, VRef B, double2* X, int nrhs) {
         XC.c1 = P<double2>(C.sc) + S_C1 * nrhs;
         XC.c2 = P<double2>(C.sc) + S_C2 * nrhs;
     }
-    switch (L.g) {
-        case 1: launch_post<1>(L, B, XC, X, nrhs, s); break;
-        case 2: launch_post<2>(L, B, XC, X, nrhs, s); break;
-        case 4: launch_post<4>(L, B, XC, X, nrhs, s); break;
-        case 8: launch_post<8>(L, B, XC, X, nrhs, s); break;
-        case 16: launch_post<16>(L, B, XC, X, nrhs, s); break;
-        default: launch_post<32>(L, B, XC, X, nrhs, s); break;
+    const Geo qr = geo(L.n, L.per_row, nrhs);
+    switch (qr.G) {
+        case 1: launch_post<1>(L, B, XC, X, nrhs, qr.grid, s); break;
+        case 2: launch_post<2>(L, B, XC, X, nrhs, qr.grid, s); break;
+        case 4: launch_post<4>(L, B, XC, X, nrhs, qr.grid, s); break;
+        case 8: launch_post<8>(L, B, XC, X, nrhs, qr.grid, s); break;
+        case 16: launch_post<16>(L, B, XC, X, nrhs, qr.grid, s); break;
+        default: launch_post<32>(L, B, XC, X, nrhs, qr.grid, s); break;
     }
 }
 
@@ -643,6 +694,8 @@ void amg_dev_destroy(void* d) { delete static_cast<DevAmg*>(d); }
 // b = S^{-1} e on the device for nb complex right-hand sides e[rhs][nf]
 // (double2, device); right-hand side r belongs to frequency r / per_freq.
 int precond_schur_solve_dev(Handle* h, int nb, int per_freq, const void* e_dev, void* b_dev) {
+    if (per_freq < 1 || per_freq > kMaxRhs)
+        return set_err(h, SVH_ERR_ARG, "preconditioner: the device AMG takes 1 to 64 right-hand sides per frequency");
     const int nfreq = nb / per_freq;
     for (int f = 0; f < nfreq; ++f) {
         void*& slot = precond_dev(h, f);
@@ -666,8 +719,9 @@ int precond_schur_solve_dev(Handle* h, int nb, int per_freq, const void* e_dev, 
         double2* x = P<double2>(D.fx);
         double2* r = P<double2>(D.fr);
         double2* fs = P<double2>(D.fs);
-        const unsigned g = nblk(n);
-        k_fcg_init<<<dim3(g, nrhs), TPB, 0, s>>>(n, e, x, r, P<double2>(D.fpart), P<unsigned>(D.fcnt), fs, nrhs);
+        const unsigned g1 = geo(n, 1, nrhs).grid;       // one lane per (row, rhs), grid-striding
+        const Geo gs = geo(n, L0.per_row, nrhs);         // the level-0 product
+        k_fcg_init<<<g1, TPB, 0, s>>>(n, nrhs, e, x, r, P<double2>(D.fpart), P<unsigned>(D.fcnt), fs);
         const double tol2 = A.tol * A.tol;
         // iteration `it` uses (p, q) = (fp, fq) when it is even, (fpo, fqo) when
         // odd; iterations after the first are replayed from one CUDA graph per
@@ -677,23 +731,22 @@ int precond_schur_solve_dev(Handle* h, int nb, int per_freq, const void* e_dev, 
             if (it & 1) { std::swap(p, po); std::swap(q, qo); }
             double2* z = P<double2>(D.fz);
             if (D.lv.size() == 1) {
-                k_dense<<<dim3((n + 7) / 8, nrhs), 256, 0, s>>>(n, P<double>(D.cinv), r, z);
+                dense(D, r, z, nrhs, s);
             } else {
                 kcycle(h, D, 0, VRef{r, nullptr, nullptr}, z, nrhs);
             }
             if (it > 0)
-                k_fcg_beta<<<dim3(g, nrhs), TPB, 0, s>>>(n, z, qo, P<double2>(D.fpart), P<unsigned>(D.fcnt), fs, nrhs);
-            k_fcg_dir<<<dim3(g, nrhs), TPB, 0, s>>>(n, z, po, p, fs, nrhs, it == 0);
-            switch (L0.g) {
-                case 1: launch_fcg_spmv<1>(L0, p, r, q, D, nrhs, s); break;
-                case 2: launch_fcg_spmv<2>(L0, p, r, q, D, nrhs, s); break;
-                case 4: launch_fcg_spmv<4>(L0, p, r, q, D, nrhs, s); break;
-                case 8: launch_fcg_spmv<8>(L0, p, r, q, D, nrhs, s); break;
-                case 16: launch_fcg_spmv<16>(L0, p, r, q, D, nrhs, s); break;
-                default: launch_fcg_spmv<32>(L0, p, r, q, D, nrhs, s); break;
+                k_fcg_beta<<<g1, TPB, 0, s>>>(n, nrhs, z, qo, P<double2>(D.fpart), P<unsigned>(D.fcnt), fs);
+            k_fcg_dir<<<nblk((int64_t)n * nrhs), TPB, 0, s>>>((int64_t)n * nrhs, nrhs, z, po, p, fs, it == 0);
+            switch (gs.G) {
+                case 1: launch_fcg_spmv<1>(L0, p, r, q, D, nrhs, gs.grid, s); break;
+                case 2: launch_fcg_spmv<2>(L0, p, r, q, D, nrhs, gs.grid, s); break;
+                case 4: launch_fcg_spmv<4>(L0, p, r, q, D, nrhs, gs.grid, s); break;
+                case 8: launch_fcg_spmv<8>(L0, p, r, q, D, nrhs, gs.grid, s); break;
+                case 16: launch_fcg_spmv<16>(L0, p, r, q, D, nrhs, gs.grid, s); break;
+                default: launch_fcg_spmv<32>(L0, p, r, q, D, nrhs, gs.grid, s); break;
             }
-            k_fcg_update<<<dim3(g, nrhs), TPB, 0, s>>>(n, p, q, x, r, P<double2>(D.fpart), P<unsigned>(D.fcnt), fs,
-                                                        nrhs, tol2);
+            k_fcg_update<<<g1, TPB, 0, s>>>(n, nrhs, p, q, x, r, P<double2>(D.fpart), P<unsigned>(D.fcnt), fs, tol2);
         };
         if (D.graph_nrhs != nrhs || D.graph_tol2 != tol2) {
             for (int k = 0; k < 2; ++k)
@@ -737,8 +790,8 @@ int precond_schur_solve_dev(Handle* h, int nb, int per_freq, const void* e_dev, 
             iters += c.x + c.y;
         }
         precond_count(h, f, 2 * nrhs, (long long)iters);
-        SVH_CUDA_TRY(h, cudaMemcpyAsync(static_cast<double2*>(b_dev) + (int64_t)f * per_freq * n, x,
-                                        (size_t)nrhs * n * 16, cudaMemcpyDeviceToDevice, s));
+        k_fcg_out<<<nblk((int64_t)n * nrhs), TPB, 0, s>>>(n, nrhs, x,
+                                                          static_cast<double2*>(b_dev) + (int64_t)f * per_freq * n);
         SVH_CUDA_TRY(h, cudaEventRecord(D.ev_out, s));              // the caller's stream waits for b
         SVH_CUDA_TRY(h, cudaStreamWaitEvent(h->stream, D.ev_out, 0));
     }

@@ -3,10 +3,12 @@
 // A batch borrows handles that each hold one structure (grid, ports, kernel
 // spectra). svh_batch_matvec applies every structure's operator to its own
 // vectors: on the first call with a given argument set the launch sequences
-// of all structures are captured from the batch stream into one CUDA graph,
-// and that call and every later call with the same arguments replay it as a
-// single graph launch (no per-kernel launch overhead for the hundreds of
-// small kernels of a batch of small grids). svh_batch_solve solves every
+// of all structures are captured into one CUDA graph, and that call and every
+// later call with the same arguments replay it as a single graph launch (no
+// per-kernel launch overhead for the hundreds of small kernels of a batch of
+// small grids). The structures are spread over up to 16 lanes (streams forked
+// from and joined to the batch stream), so the graph holds independent chains
+// and the small products of different structures run concurrently. svh_batch_solve solves every
 // structure's ports at the given frequencies with worker threads, each
 // driving one structure at a time on its own stream, so that the host AMG of
 // one structure overlaps the device work of the others.
@@ -27,6 +29,10 @@ namespace svh {
 struct Batch {
     int device = 0;
     cudaStream_t stream = nullptr;    // capture / replay stream (owned)
+    static constexpr int kLanes = 16;
+    std::vector<cudaStream_t> lanes;  // structure i runs on lanes[i % lanes.size()]
+    std::vector<cudaEvent_t> lane_done;
+    cudaEvent_t fork = nullptr;
     std::vector<Handle*> items;
     std::string err;
     // captured product
@@ -48,6 +54,47 @@ struct Batch {
 static int berr(Batch* b, int code, const std::string& m) {
     b->err = m;
     return code;
+}
+
+static bool ensure_lanes(Batch* b) {
+    const size_t want = std::min<size_t>(Batch::kLanes, std::max<size_t>(1, b->items.size()));
+    if (!b->fork && cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) return false;
+    while (b->lanes.size() < want) {
+        cudaStream_t st;
+        cudaEvent_t ev;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return false;
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+            cudaStreamDestroy(st);
+            return false;
+        }
+        b->lanes.push_back(st);
+        b->lane_done.push_back(ev);
+    }
+    return true;
+}
+
+// every structure's product on its lane, forked from and joined to the batch stream
+static int launch_all(Batch* b, const double* omegas, int nb, const void* const* x_dev, void* const* y_dev,
+                      int precision, std::string& msg) {
+    const size_t n = b->items.size(), L = std::min(b->lanes.size(), n);
+    if (cudaEventRecord(b->fork, b->stream) != cudaSuccess) return SVH_ERR_CUDA;
+    for (size_t l = 0; l < L; ++l)
+        if (cudaStreamWaitEvent(b->lanes[l], b->fork, 0) != cudaSuccess) return SVH_ERR_CUDA;
+    int rc = SVH_OK;
+    for (size_t i = 0; i < n && rc == SVH_OK; ++i) {
+        Handle* h = b->items[i];
+        cudaStream_t saved = h->stream;
+        h->stream = b->lanes[i % L];
+        rc = precision == SVH_FP32 ? launch_matvec32(h, omegas[i], nb, x_dev[i], y_dev[i], 0)
+                                   : launch_matvec64(h, omegas[i], nb, x_dev[i], y_dev[i], 0);
+        if (rc) msg = h->err;
+        h->stream = saved;
+    }
+    for (size_t l = 0; l < L; ++l) {
+        cudaEventRecord(b->lane_done[l], b->lanes[l]);
+        cudaStreamWaitEvent(b->stream, b->lane_done[l], 0);
+    }
+    return rc;
 }
 
 }  // namespace svh
@@ -77,6 +124,9 @@ int svh_batch_destroy(svh_batch* bb) {
     cudaSetDevice(b->device);
     cudaStreamSynchronize(b->stream);
     b->drop_graph();
+    for (cudaStream_t st : b->lanes) cudaStreamDestroy(st);
+    for (cudaEvent_t e : b->lane_done) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
     cudaStreamDestroy(b->stream);
     delete b;
     return SVH_OK;
@@ -121,45 +171,30 @@ int svh_batch_matvec(svh_batch* bb, const double* omegas, int nb, const void* co
                       std::equal(b->key_om.begin(), b->key_om.end(), omegas);
     if (!same) {
         b->drop_graph();
+        if (!ensure_lanes(b)) return berr(b, SVH_ERR_CUDA, "svh_batch_matvec: stream set-up failed");
         // run once eagerly so that every buffer a product needs exists before capture
-        std::vector<cudaStream_t> saved(n);
-        for (size_t i = 0; i < n; ++i) {
-            Handle* h = b->items[i];
-            saved[i] = h->stream;
-            h->stream = b->stream;
-            int rc = precision == SVH_FP32 ? launch_matvec32(h, omegas[i], nb, x_dev[i], y_dev[i], 0)
-                                           : launch_matvec64(h, omegas[i], nb, x_dev[i], y_dev[i], 0);
-            if (rc) {
-                for (size_t k = 0; k <= i; ++k) b->items[k]->stream = saved[k];
-                return berr(b, rc, std::string("svh_batch_matvec: item product failed: ") + h->err);
-            }
-        }
-        if (cudaStreamSynchronize(b->stream) != cudaSuccess) {
-            for (size_t k = 0; k < n; ++k) b->items[k]->stream = saved[k];
-            return berr(b, SVH_ERR_CUDA, "svh_batch_matvec: eager run failed");
-        }
+        std::string msg;
+        int rc = launch_all(b, omegas, nb, x_dev, y_dev, precision, msg);
+        if (rc) return berr(b, rc, std::string("svh_batch_matvec: item product failed: ") + msg);
+        if (cudaStreamSynchronize(b->stream) != cudaSuccess) return berr(b, SVH_ERR_CUDA, "svh_batch_matvec: eager run failed");
         cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeRelaxed);
-        int rc = SVH_OK;
         if (e == cudaSuccess) {
-            for (size_t i = 0; i < n && rc == SVH_OK; ++i) {
-                Handle* h = b->items[i];
-                rc = precision == SVH_FP32 ? launch_matvec32(h, omegas[i], nb, x_dev[i], y_dev[i], 0)
-                                           : launch_matvec64(h, omegas[i], nb, x_dev[i], y_dev[i], 0);
-            }
+            rc = launch_all(b, omegas, nb, x_dev, y_dev, precision, msg);
             cudaGraph_t g = nullptr;
             cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
             if (e2 == cudaSuccess && rc == SVH_OK) {
                 b->graph = g;
                 e2 = cudaGraphInstantiate(&b->exec, g, 0);
+            } else if (g) {
+                cudaGraphDestroy(g);
             }
             if (e2 != cudaSuccess) e = e2;
         }
-        for (size_t k = 0; k < n; ++k) b->items[k]->stream = saved[k];
         if (e != cudaSuccess || rc != SVH_OK) {
             b->drop_graph();
             cudaGetLastError();
             return berr(b, rc ? rc : SVH_ERR_CUDA, std::string("svh_batch_matvec: graph capture failed: ") +
-                                                       cudaGetErrorString(e));
+                                                       (rc ? msg : std::string(cudaGetErrorString(e))));
         }
         b->key_x.assign(x_dev, x_dev + n);
         b->key_y.assign(y_dev, y_dev + n);

@@ -80,6 +80,22 @@ static int fft_size(int K) {
     return n;
 }
 
+// Default padded size of an axis: any P >= 2K - 1 embeds the convolution
+// exactly, so take the smallest size that has size-specialised kernels (x, y:
+// 16 .. 1024; z: 8 .. 48), else the smallest 2,3,5,7-smooth size (2K first).
+static int default_fft_size(int K, bool zaxis) {
+    static const int xy[] = {16, 32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024};
+    static const int zz[] = {8, 12, 16, 24, 32, 48};
+    if (zaxis) {
+        for (int p : zz)
+            if (p >= 2 * K - 1) return p;
+    } else {
+        for (int p : xy)
+            if (p >= 2 * K - 1) return p;
+    }
+    return fft_size(K);
+}
+
 static FftPlanHost make_plan(int N) {
     FftPlanHost p;
     p.N = N;
@@ -624,7 +640,7 @@ int svh_setup_grid(svh_handle* hh, int Kx, int Ky, int Kz, double dx, const uint
         for (int y = 0; y < Ky; ++y)
             if (rowmask[(size_t)zi * Ky + y]) h->rows.push_back(zi * Ky + y);
     }
-    h->Px = fft_size(Kx); h->Py = fft_size(Ky); h->Pz = fft_size(Kz);
+    h->Px = default_fft_size(Kx, false); h->Py = default_fft_size(Ky, false); h->Pz = default_fft_size(Kz, true);
     h->Hx = h->Px / 2 + 1; h->Hy = h->Py / 2 + 1; h->Hz = h->Pz / 2 + 1;
     std::vector<uint8_t> freem(M);
     for (int64_t m = 0; m < M; ++m) freem[m] = h->fixed[m] ? 0 : 1;

@@ -76,7 +76,7 @@ def test_strip_matvec_vs_dense_oracle(prec):
 
 @pytest.mark.parametrize("seed,shape,P", [
     (21, (13, 9, 5), None),          # ragged, P = 26, 18, 10
-    (22, (37, 11, 3), None),         # 2*37 not smooth -> P = 75 = 3*5*5
+    (22, (37, 11, 3), (75, 21, 6)),  # 2*37, 2*11 not smooth: the oracle's P (generic kernels)
     (23, (24, 20, 6), (48, 40, 12)),
     (24, (10, 14, 7), (21, 27, 14)),  # odd FFT sizes 2K - 1 (radix 3 and 7)
     (25, (70, 33, 4), None),         # several x-lines per block, ragged y tiles
