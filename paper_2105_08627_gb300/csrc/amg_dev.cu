@@ -22,7 +22,12 @@
 //   * dot products finish in the last block to complete, summing the block
 //     partials in index order (results do not depend on block scheduling);
 //   * the coarsest level is solved by its dense inverse (from the host
-//     Cholesky factor): one matrix-vector product.
+//     Cholesky factor): one matrix-vector product;
+//   * the K-cycle is a preconditioner inside flexible CG, so it runs in FP32
+//     (matrices, vectors and arithmetic; its dot products accumulate in
+//     FP64), while the CG itself (S p, residuals, iterates) stays FP64: the
+//     cycle's gathers move half the bytes and its arithmetic avoids the slow
+//     FP64 units of this GPU.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -43,23 +48,35 @@ __device__ __forceinline__ double2 sub2(double2 a, double2 b) { return d2(a.x - 
 __device__ __forceinline__ double2 mul(double2 a, double2 b) { return d2(a.x * b.x, a.y * b.y); }
 __device__ __forceinline__ double2 scl(double s, double2 a) { return d2(s * a.x, s * a.y); }
 
+// FP32 pairs: the K-cycle (a preconditioner inside flexible CG) runs in FP32
+// data and arithmetic; its dot products accumulate in FP64
+__device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
+__device__ __forceinline__ float2 fadd(float2 a, float2 b) { return f2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 fsub(float2 a, float2 b) { return f2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 fmul(float2 a, float2 b) { return f2(a.x * b.x, a.y * b.y); }
+__device__ __forceinline__ float2 fscl(float s, float2 a) { return f2(s * a.x, s * a.y); }
+__device__ __forceinline__ float2 tof(double2 a) { return f2((float)a.x, (float)a.y); }
+__device__ __forceinline__ double2 dprod(float2 a, float2 b) {
+    return d2((double)a.x * (double)b.x, (double)a.y * (double)b.y);
+}
+
 // a right-hand side read on the fly: b - coef * w (w may be null)
 struct VRef {
-    const double2* b;
-    const double2* w;
+    const float2* b;
+    const float2* w;
     const double2* coef;   // [nrhs]
 };
 
-__device__ __forceinline__ double2 vget(const VRef& B, int64_t off, double2 cf) {
-    double2 v = B.b[off];
-    if (B.w) v = sub2(v, mul(cf, B.w[off]));
+__device__ __forceinline__ float2 vget(const VRef& B, int64_t off, float2 cf) {
+    float2 v = B.b[off];
+    if (B.w) v = fsub(v, fmul(cf, B.w[off]));
     return v;
 }
 
 // the coarse correction read on the fly: v1 (plain) or c1 v1 + c2 v2
 struct XRef {
-    const double2* v1;
-    const double2* v2;
+    const float2* v1;
+    const float2* v2;
     const double2* c1;     // [nrhs] or null (plain)
     const double2* c2;
 };
@@ -150,8 +167,8 @@ __device__ bool block_sums_last(const double2 (&val)[ND], int G, int nrhs, doubl
 // long Galerkin rows): lane `sub` takes the row's entries sub, sub + G, ...;
 // the group's partial sums meet in one shuffle reduction after the loops
 // (every lane reaches it, so the shuffles stay convergent).
-template <int G>
-__device__ __forceinline__ double2 group_sum(double2 v) {
+template <int G, typename V>
+__device__ __forceinline__ V group_sum(V v) {
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) {
         v.x += __shfl_down_sync(0xffffffffu, v.x, o, G);
@@ -160,9 +177,9 @@ __device__ __forceinline__ double2 group_sum(double2 v) {
     return v;   // complete in the group's lane 0
 }
 
-__device__ __forceinline__ double2 xcget(const XRef& X, int64_t idx, int r) {
+__device__ __forceinline__ float2 xcget(const XRef& X, int64_t idx, float2 c1, float2 c2) {
     if (!X.c1) return X.v1[idx];
-    return add(mul(X.c1[r], X.v1[idx]), mul(X.c2[r], X.v2[idx]));
+    return fadd(fmul(c1, X.v1[idx]), fmul(c2, X.v2[idx]));
 }
 
 // K-cycle, first half: x0 = b / l1 (one l1-Jacobi sweep from zero), the
@@ -170,22 +187,22 @@ __device__ __forceinline__ double2 xcget(const XRef& X, int64_t idx, int r) {
 // one lane group per (aggregate, rhs).
 template <int G>
 __global__ void __launch_bounds__(TPB) k_kc_pre(int n, int nc, int nrhs, const int* __restrict__ rp,
-                                                const int* __restrict__ ci, const double* __restrict__ v,
-                                                const double* __restrict__ l1inv, const int* __restrict__ crp,
-                                                const int* __restrict__ cidx, VRef B, double2* __restrict__ rc) {
+                                                const int* __restrict__ ci, const float* __restrict__ v,
+                                                const float* __restrict__ l1inv, const int* __restrict__ crp,
+                                                const int* __restrict__ cidx, VRef B, float2* __restrict__ rc) {
     const Lanes L = lanes(G, nrhs);
-    const double2 cf = B.w ? B.coef[L.rhs] : d2(0, 0);
+    const float2 cf = B.w ? tof(B.coef[L.rhs]) : f2(0, 0);
     for (int64_t ub = blockIdx.x; ub * L.U < nc; ub += gridDim.x) {
         const int64_t c = ub * L.U + L.uloc;
         const bool act = L.live && c < nc;
-        double2 s = d2(0, 0);
+        float2 s = f2(0, 0);
         if (act) {
             for (int p = crp[c]; p < crp[c + 1]; ++p) {
                 const int i = cidx[p];
-                if (L.sub == 0) s = add(s, vget(B, (int64_t)i * nrhs + L.rhs, cf));
+                if (L.sub == 0) s = fadd(s, vget(B, (int64_t)i * nrhs + L.rhs, cf));
                 for (int q = rp[i] + L.sub; q < rp[i + 1]; q += G) {
                     const int j = ci[q];
-                    s = sub2(s, scl(v[q] * l1inv[j], vget(B, (int64_t)j * nrhs + L.rhs, cf)));
+                    s = fsub(s, fscl(v[q] * l1inv[j], vget(B, (int64_t)j * nrhs + L.rhs, cf)));
                 }
             }
         }
@@ -198,45 +215,46 @@ __global__ void __launch_bounds__(TPB) k_kc_pre(int n, int nc, int nrhs, const i
 // l1-Jacobi sweep x = x1 + (b - A x1) / l1; one lane group per (row, rhs).
 template <int G>
 __global__ void __launch_bounds__(TPB) k_kc_post(int n, int nrhs, const int* __restrict__ rp,
-                                                 const int* __restrict__ ci, const double* __restrict__ v,
-                                                 const double* __restrict__ l1inv, const int* __restrict__ agg, VRef B,
-                                                 XRef XC, double2* __restrict__ X) {
+                                                 const int* __restrict__ ci, const float* __restrict__ v,
+                                                 const float* __restrict__ l1inv, const int* __restrict__ agg, VRef B,
+                                                 XRef XC, float2* __restrict__ X) {
     const Lanes L = lanes(G, nrhs);
-    const double2 cf = B.w ? B.coef[L.rhs] : d2(0, 0);
+    const float2 cf = B.w ? tof(B.coef[L.rhs]) : f2(0, 0);
+    const float2 c1 = XC.c1 ? tof(XC.c1[L.rhs]) : f2(1, 1), c2 = XC.c2 ? tof(XC.c2[L.rhs]) : f2(0, 0);
     for (int64_t ub = blockIdx.x; ub * L.U < n; ub += gridDim.x) {
         const int64_t i = ub * L.U + L.uloc;
         const bool act = L.live && i < n;
-        double2 ax = d2(0, 0);
+        float2 ax = f2(0, 0);
         if (act) {
             for (int q = rp[i] + L.sub; q < rp[i + 1]; q += G) {
                 const int j = ci[q];
                 const int64_t jx = (int64_t)j * nrhs + L.rhs;
-                const double2 xj = add(scl(l1inv[j], vget(B, jx, cf)), xcget(XC, (int64_t)agg[j] * nrhs + L.rhs, L.rhs));
-                ax = add(ax, scl(v[q], xj));
+                const float2 xj = fadd(fscl(l1inv[j], vget(B, jx, cf)), xcget(XC, (int64_t)agg[j] * nrhs + L.rhs, c1, c2));
+                ax = fadd(ax, fscl(v[q], xj));
             }
         }
         ax = group_sum<G>(ax);
         if (act && L.sub == 0) {
             const int64_t ix = i * nrhs + L.rhs;
-            const double2 bi = vget(B, ix, cf);
-            const double2 xi = add(scl(l1inv[i], bi), xcget(XC, (int64_t)agg[i] * nrhs + L.rhs, L.rhs));
-            X[ix] = add(xi, scl(l1inv[i], sub2(bi, ax)));
+            const float2 bi = vget(B, ix, cf);
+            const float2 xi = fadd(fscl(l1inv[i], bi), xcget(XC, (int64_t)agg[i] * nrhs + L.rhs, c1, c2));
+            X[ix] = fadd(xi, fscl(l1inv[i], fsub(bi, ax)));
         }
     }
 }
 
 // coarsest level: X = C^{-1} b, one warp per (row, rhs)
-__global__ void k_dense(int n, int nrhs, const double* __restrict__ cinv, const double2* __restrict__ b,
-                        double2* __restrict__ X) {
+__global__ void k_dense(int n, int nrhs, const float* __restrict__ cinv, const float2* __restrict__ b,
+                        float2* __restrict__ X) {
     const int64_t w = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (w >= (int64_t)n * nrhs) return;
     const int row = (int)(w / nrhs), r = (int)(w % nrhs);
-    const double* cr = cinv + (int64_t)row * n;
-    double x = 0, y = 0;
+    const float* cr = cinv + (int64_t)row * n;
+    float x = 0, y = 0;
     for (int j = lane; j < n; j += 32) {
-        const double c = cr[j];
-        const double2 bj = b[(int64_t)j * nrhs + r];
+        const float c = cr[j];
+        const float2 bj = b[(int64_t)j * nrhs + r];
         x += c * bj.x;
         y += c * bj.y;
     }
@@ -245,7 +263,7 @@ __global__ void k_dense(int n, int nrhs, const double* __restrict__ cinv, const 
         x += __shfl_down_sync(0xffffffffu, x, o);
         y += __shfl_down_sync(0xffffffffu, y, o);
     }
-    if (lane == 0) X[(int64_t)row * nrhs + r] = d2(x, y);
+    if (lane == 0) X[(int64_t)row * nrhs + r] = f2(x, y);
 }
 
 // w = A vin with dot products; MODE 1 (first Krylov step): d11 = v1.w,
@@ -253,9 +271,9 @@ __global__ void k_dense(int n, int nrhs, const double* __restrict__ cinv, const 
 // g2 = v2.b -> (c1, c2) minimising the A-norm of the error over span{v1, v2}.
 template <int MODE, int G>
 __global__ void __launch_bounds__(TPB) k_kc_spmv(int n, int nrhs, const int* __restrict__ rp,
-                                                 const int* __restrict__ ci, const double* __restrict__ v,
-                                                 const double2* __restrict__ vin, const double2* __restrict__ v1,
-                                                 const double2* __restrict__ b, double2* __restrict__ w,
+                                                 const int* __restrict__ ci, const float* __restrict__ v,
+                                                 const float2* __restrict__ vin, const float2* __restrict__ v1,
+                                                 const float2* __restrict__ b, float2* __restrict__ w,
                                                  double2* part, unsigned* cnt, double2* sc) {
     constexpr int ND = MODE == 1 ? 2 : 3;
     __shared__ double2 tot[64 * ND];
@@ -266,22 +284,22 @@ __global__ void __launch_bounds__(TPB) k_kc_spmv(int n, int nrhs, const int* __r
     for (int64_t ub = blockIdx.x; ub * L.U < n; ub += gridDim.x) {
         const int64_t i = ub * L.U + L.uloc;
         const bool act = L.live && i < n;
-        double2 ax = d2(0, 0);
+        float2 ax = f2(0, 0);
         if (act)
             for (int q = rp[i] + L.sub; q < rp[i + 1]; q += G)
-                ax = add(ax, scl(v[q], vin[(int64_t)ci[q] * nrhs + L.rhs]));
+                ax = fadd(ax, fscl(v[q], vin[(int64_t)ci[q] * nrhs + L.rhs]));
         ax = group_sum<G>(ax);
         if (act && L.sub == 0) {
             const int64_t ix = i * nrhs + L.rhs;
             w[ix] = ax;
-            const double2 vi = vin[ix], bi = b[ix];
+            const float2 vi = vin[ix], bi = b[ix];
             if (MODE == 1) {
-                val[0] = add(val[0], mul(vi, ax));
-                val[1] = add(val[1], mul(vi, bi));
+                val[0] = add(val[0], dprod(vi, ax));
+                val[1] = add(val[1], dprod(vi, bi));
             } else {
-                val[0] = add(val[0], mul(v1[ix], ax));
-                val[1] = add(val[1], mul(vi, ax));
-                val[2] = add(val[2], mul(vi, bi));
+                val[0] = add(val[0], dprod(v1[ix], ax));
+                val[1] = add(val[1], dprod(vi, ax));
+                val[2] = add(val[2], dprod(vi, bi));
             }
         }
     }
@@ -437,6 +455,16 @@ __global__ void __launch_bounds__(TPB) k_fcg_update(int n, int nrhs, const doubl
     }
 }
 
+// the K-cycle's FP32 input (r) and FP64 output (z)
+__global__ void k_to_f32(int64_t total, const double2* __restrict__ a, float2* __restrict__ b) {
+    const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (o < total) b[o] = tof(a[o]);
+}
+__global__ void k_to_f64(int64_t total, const float2* __restrict__ a, double2* __restrict__ b) {
+    const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (o < total) b[o] = d2(a[o].x, a[o].y);
+}
+
 // solution out in the caller's [rhs][n] layout
 __global__ void k_fcg_out(int n, int nrhs, const double2* __restrict__ x, double2* __restrict__ b) {
     const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -451,8 +479,9 @@ struct DLevel {
     int n = 0, nc = 0;
     double per_row = 1, per_agg = 1;   // mean entries per row, and per aggregate (restriction)
     bool krylov = true;          // coarse solves on this level take the two Krylov steps
-    DevBuf rp, ci, v, l1inv, agg, crp, cidx;
-    DevBuf v1, w1, v2, w2, rc;   // [n][nrhs] (rc: [nc][nrhs])
+    DevBuf rp, ci, v, agg, crp, cidx;   // v: FP64 values (the top-level CG product, level 0)
+    DevBuf vf, l1f;                      // FP32 values and l1 norms for the K-cycle
+    DevBuf v1, w1, v2, w2, rc;           // FP32 [n][nrhs] (rc: [nc][nrhs])
     DevBuf sc, part, cnt;        // scalar slots, block partials, completion counters
 };
 
@@ -460,7 +489,8 @@ struct DevAmg {
     std::vector<DLevel> lv;
     DevBuf cinv;                 // dense inverse of the coarsest operator
     int nrhs = 0;                // capacity of the workspaces
-    DevBuf fx, fr, fz, fp, fq, fpo, fqo, fs, fpart, fcnt;   // top-level CG
+    DevBuf fx, fr, fz, fp, fq, fpo, fqo, fs, fpart, fcnt;   // top-level CG (FP64)
+    DevBuf kr, kz;               // FP32 K-cycle input (r) and output (z)
     double2* host_fs = nullptr;  // pinned copy of the CG slots
     cudaGraphExec_t ge[2] = {nullptr, nullptr};   // one CG iteration per parity
     int graph_nrhs = 0;
@@ -476,10 +506,10 @@ struct DevAmg {
         for (cudaGraphExec_t g : ge)
             if (g) cudaGraphExecDestroy(g);
         for (DLevel& L : lv)
-            for (DevBuf* b : {&L.rp, &L.ci, &L.v, &L.l1inv, &L.agg, &L.crp, &L.cidx, &L.v1, &L.w1, &L.v2, &L.w2,
-                              &L.rc, &L.sc, &L.part, &L.cnt})
+            for (DevBuf* b : {&L.rp, &L.ci, &L.v, &L.vf, &L.l1f, &L.agg, &L.crp, &L.cidx, &L.v1, &L.w1, &L.v2,
+                              &L.w2, &L.rc, &L.sc, &L.part, &L.cnt})
                 dev_free(*b);
-        for (DevBuf* b : {&cinv, &fx, &fr, &fz, &fp, &fq, &fpo, &fqo, &fs, &fpart, &fcnt}) dev_free(*b);
+        for (DevBuf* b : {&cinv, &fx, &fr, &fz, &fp, &fq, &fpo, &fqo, &fs, &fpart, &fcnt, &kr, &kz}) dev_free(*b);
         if (host_fs) cudaFreeHost(host_fs);
     }
 };
@@ -525,12 +555,13 @@ int upload(Handle* h, DevAmg& D, const AmgView& A) {
         // small levels (latency-bound launches) one cycle is cheaper overall
         L.krylov = V.n >= kKrylovMinRows;
         L.per_agg = L.nc > 0 ? (double)nnz / L.nc : 1;
-        std::vector<double> inv(V.n);
-        for (int i = 0; i < V.n; ++i) inv[i] = 1.0 / V.l1[i];
+        std::vector<float> inv(V.n), vf(V.v, V.v + nnz);
+        for (int i = 0; i < V.n; ++i) inv[i] = (float)(1.0 / V.l1[i]);
         int rc;
         if ((rc = dev_upload(h, L.rp, V.rp, (size_t)(V.n + 1) * 4)) || (rc = dev_upload(h, L.ci, V.ci, (size_t)nnz * 4)) ||
-            (rc = dev_upload(h, L.v, V.v, (size_t)nnz * 8)) || (rc = dev_upload(h, L.l1inv, inv.data(), inv.size() * 8)))
+            (rc = dev_upload(h, L.vf, vf.data(), (size_t)nnz * 4)) || (rc = dev_upload(h, L.l1f, inv.data(), inv.size() * 4)))
             return rc;
+        if (l == 0 && (rc = dev_upload(h, L.v, V.v, (size_t)nnz * 8))) return rc;
         if (L.nc > 0) {
             if ((rc = dev_upload(h, L.agg, V.agg, (size_t)V.n * 4)) ||
                 (rc = dev_upload(h, L.crp, V.crp, (size_t)(L.nc + 1) * 4)) ||
@@ -555,7 +586,8 @@ int upload(Handle* h, DevAmg& D, const AmgView& A) {
         }
         for (int i = 0; i < n; ++i) inv[(size_t)i * n + j] = col[i];
     }
-    return dev_upload(h, D.cinv, inv.data(), inv.size() * 8);
+    std::vector<float> invf(inv.begin(), inv.end());
+    return dev_upload(h, D.cinv, invf.data(), invf.size() * 4);
 }
 
 int ensure_work(Handle* h, DevAmg& D, int nrhs) {
@@ -565,9 +597,9 @@ int ensure_work(Handle* h, DevAmg& D, int nrhs) {
     D.graph_nrhs = 0;
     int rc;
     for (DLevel& L : D.lv) {
-        const size_t vb = (size_t)nrhs * L.n * 16;
+        const size_t vb = (size_t)nrhs * L.n * 8;
         if ((rc = dev_alloc(h, L.v1, vb)) || (rc = dev_alloc(h, L.w1, vb)) || (rc = dev_alloc(h, L.v2, vb)) ||
-            (rc = dev_alloc(h, L.w2, vb)) || (rc = dev_alloc(h, L.rc, (size_t)nrhs * (L.nc > 0 ? L.nc : 1) * 16)) ||
+            (rc = dev_alloc(h, L.w2, vb)) || (rc = dev_alloc(h, L.rc, (size_t)nrhs * (L.nc > 0 ? L.nc : 1) * 8)) ||
             (rc = dev_alloc(h, L.sc, (size_t)NSLOT * nrhs * 16)) ||
             (rc = dev_alloc(h, L.part, (size_t)nrhs * kMaxGrid * 3 * 16)) || (rc = dev_alloc(h, L.cnt, 4)))
             return rc;
@@ -578,7 +610,8 @@ int ensure_work(Handle* h, DevAmg& D, int nrhs) {
     if ((rc = dev_alloc(h, D.fx, vb)) || (rc = dev_alloc(h, D.fr, vb)) || (rc = dev_alloc(h, D.fz, vb)) ||
         (rc = dev_alloc(h, D.fp, vb)) || (rc = dev_alloc(h, D.fq, vb)) || (rc = dev_alloc(h, D.fpo, vb)) ||
         (rc = dev_alloc(h, D.fqo, vb)) || (rc = dev_alloc(h, D.fs, (size_t)NFSLOT * nrhs * 16)) ||
-        (rc = dev_alloc(h, D.fpart, (size_t)nrhs * kMaxGrid * 2 * 16)) || (rc = dev_alloc(h, D.fcnt, 4)))
+        (rc = dev_alloc(h, D.fpart, (size_t)nrhs * kMaxGrid * 2 * 16)) || (rc = dev_alloc(h, D.fcnt, 4)) ||
+        (rc = dev_alloc(h, D.kr, (size_t)nrhs * D.lv[0].n * 8)) || (rc = dev_alloc(h, D.kz, (size_t)nrhs * D.lv[0].n * 8)))
         return rc;
     SVH_CUDA_TRY(h, cudaMemsetAsync(D.fcnt.p, 0, 4, D.st));
     if (D.host_fs) cudaFreeHost(D.host_fs);
@@ -588,29 +621,29 @@ int ensure_work(Handle* h, DevAmg& D, int nrhs) {
     return SVH_OK;
 }
 
-void kcycle(Handle* h, DevAmg& D, int l, VRef B, double2* X, int nrhs);
+void kcycle(Handle* h, DevAmg& D, int l, VRef B, float2* X, int nrhs);
 
 template <int G>
 void launch_pre(DLevel& L, VRef B, int nrhs, unsigned grid, cudaStream_t s) {
-    k_kc_pre<G><<<grid, TPB, 0, s>>>(L.n, L.nc, nrhs, P<int>(L.rp), P<int>(L.ci), P<double>(L.v), P<double>(L.l1inv),
-                                     P<int>(L.crp), P<int>(L.cidx), B, P<double2>(L.rc));
+    k_kc_pre<G><<<grid, TPB, 0, s>>>(L.n, L.nc, nrhs, P<int>(L.rp), P<int>(L.ci), P<float>(L.vf), P<float>(L.l1f),
+                                     P<int>(L.crp), P<int>(L.cidx), B, P<float2>(L.rc));
 }
 
 template <int G>
-void launch_post(DLevel& L, VRef B, XRef XC, double2* X, int nrhs, unsigned grid, cudaStream_t s) {
-    k_kc_post<G><<<grid, TPB, 0, s>>>(L.n, nrhs, P<int>(L.rp), P<int>(L.ci), P<double>(L.v), P<double>(L.l1inv),
+void launch_post(DLevel& L, VRef B, XRef XC, float2* X, int nrhs, unsigned grid, cudaStream_t s) {
+    k_kc_post<G><<<grid, TPB, 0, s>>>(L.n, nrhs, P<int>(L.rp), P<int>(L.ci), P<float>(L.vf), P<float>(L.l1f),
                                       P<int>(L.agg), B, XC, X);
 }
 
 template <int MODE, int G>
-void launch_spmv_kc(DLevel& L, const double2* vin, const double2* v1, const double2* b, double2* w, int nrhs,
+void launch_spmv_kc(DLevel& L, const float2* vin, const float2* v1, const float2* b, float2* w, int nrhs,
                     unsigned grid, cudaStream_t s) {
-    k_kc_spmv<MODE, G><<<grid, TPB, 0, s>>>(L.n, nrhs, P<int>(L.rp), P<int>(L.ci), P<double>(L.v), vin, v1, b, w,
+    k_kc_spmv<MODE, G><<<grid, TPB, 0, s>>>(L.n, nrhs, P<int>(L.rp), P<int>(L.ci), P<float>(L.vf), vin, v1, b, w,
                                             P<double2>(L.part), P<unsigned>(L.cnt), P<double2>(L.sc));
 }
 
 template <int MODE>
-void spmv_kc(DLevel& L, const double2* vin, const double2* v1, const double2* b, double2* w, int nrhs,
+void spmv_kc(DLevel& L, const float2* vin, const float2* v1, const float2* b, float2* w, int nrhs,
              cudaStream_t s) {
     const Geo q = geo(L.n, L.per_row, nrhs);
     switch (q.G) {
@@ -630,34 +663,34 @@ void launch_fcg_spmv(DLevel& L0, const double2* p, const double2* r, double2* q,
                                        P<double2>(D.fpart), P<unsigned>(D.fcnt), P<double2>(D.fs));
 }
 
-void dense(DevAmg& D, const double2* b, double2* X, int nrhs, cudaStream_t s) {
+void dense(DevAmg& D, const float2* b, float2* X, int nrhs, cudaStream_t s) {
     const int n = D.lv.back().n;
     const int64_t warps = (int64_t)n * nrhs;
-    k_dense<<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(n, nrhs, P<double>(D.cinv), b, X);
+    k_dense<<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(n, nrhs, P<float>(D.cinv), b, X);
 }
 
 // two Krylov steps on level l with the level-l cycle as preconditioner; the
 // result is c1 v1 + c2 v2 of this level (read by the caller's post kernel),
 // or v1 alone on the coarsest level
-void coarse_krylov(Handle* h, DevAmg& D, int l, const double2* b, int nrhs) {
+void coarse_krylov(Handle* h, DevAmg& D, int l, const float2* b, int nrhs) {
     DLevel& L = D.lv[l];
     cudaStream_t s = D.st;
     if (l + 1 == (int)D.lv.size()) {
-        dense(D, b, P<double2>(L.v1), nrhs, s);
+        dense(D, b, P<float2>(L.v1), nrhs, s);
         return;
     }
     if (!L.krylov) {   // small level: one cycle, no Krylov acceleration (result in v1)
-        kcycle(h, D, l, VRef{b, nullptr, nullptr}, P<double2>(L.v1), nrhs);
+        kcycle(h, D, l, VRef{b, nullptr, nullptr}, P<float2>(L.v1), nrhs);
         return;
     }
-    kcycle(h, D, l, VRef{b, nullptr, nullptr}, P<double2>(L.v1), nrhs);
-    spmv_kc<1>(L, P<double2>(L.v1), nullptr, b, P<double2>(L.w1), nrhs, s);
-    kcycle(h, D, l, VRef{b, P<double2>(L.w1), P<double2>(L.sc) + S_A1 * nrhs}, P<double2>(L.v2), nrhs);
-    spmv_kc<2>(L, P<double2>(L.v2), P<double2>(L.v1), b, P<double2>(L.w2), nrhs, s);
+    kcycle(h, D, l, VRef{b, nullptr, nullptr}, P<float2>(L.v1), nrhs);
+    spmv_kc<1>(L, P<float2>(L.v1), nullptr, b, P<float2>(L.w1), nrhs, s);
+    kcycle(h, D, l, VRef{b, P<float2>(L.w1), P<double2>(L.sc) + S_A1 * nrhs}, P<float2>(L.v2), nrhs);
+    spmv_kc<2>(L, P<float2>(L.v2), P<float2>(L.v1), b, P<float2>(L.w2), nrhs, s);
 }
 
 // X ~= A_l^{-1} B (zero initial guess), l below the coarsest level
-void kcycle(Handle* h, DevAmg& D, int l, VRef B, double2* X, int nrhs) {
+void kcycle(Handle* h, DevAmg& D, int l, VRef B, float2* X, int nrhs) {
     DLevel& L = D.lv[l];
     DLevel& C = D.lv[l + 1];
     cudaStream_t s = D.st;
@@ -670,8 +703,8 @@ void kcycle(Handle* h, DevAmg& D, int l, VRef B, double2* X, int nrhs) {
         case 16: launch_pre<16>(L, B, nrhs, qa.grid, s); break;
         default: launch_pre<32>(L, B, nrhs, qa.grid, s); break;
     }
-    coarse_krylov(h, D, l + 1, P<double2>(L.rc), nrhs);
-    XRef XC{P<double2>(C.v1), P<double2>(C.v2), nullptr, nullptr};
+    coarse_krylov(h, D, l + 1, P<float2>(L.rc), nrhs);
+    XRef XC{P<float2>(C.v1), P<float2>(C.v2), nullptr, nullptr};
     if (l + 2 < (int)D.lv.size() && C.krylov) {
         XC.c1 = P<double2>(C.sc) + S_C1 * nrhs;
         XC.c2 = P<double2>(C.sc) + S_C2 * nrhs;
@@ -730,11 +763,16 @@ int precond_schur_solve_dev(Handle* h, int nb, int per_freq, const void* e_dev, 
             double2 *p = P<double2>(D.fp), *q = P<double2>(D.fq), *po = P<double2>(D.fpo), *qo = P<double2>(D.fqo);
             if (it & 1) { std::swap(p, po); std::swap(q, qo); }
             double2* z = P<double2>(D.fz);
+            // z = K-cycle(r) in FP32 (a preconditioner: flexible CG keeps the iteration in FP64)
+            const int64_t tot = (int64_t)n * nrhs;
+            float2 *kr = P<float2>(D.kr), *kz = P<float2>(D.kz);
+            k_to_f32<<<nblk(tot), TPB, 0, s>>>(tot, r, kr);
             if (D.lv.size() == 1) {
-                dense(D, r, z, nrhs, s);
+                dense(D, kr, kz, nrhs, s);
             } else {
-                kcycle(h, D, 0, VRef{r, nullptr, nullptr}, z, nrhs);
+                kcycle(h, D, 0, VRef{kr, nullptr, nullptr}, kz, nrhs);
             }
+            k_to_f64<<<nblk(tot), TPB, 0, s>>>(tot, kz, z);
             if (it > 0)
                 k_fcg_beta<<<g1, TPB, 0, s>>>(n, nrhs, z, qo, P<double2>(D.fpart), P<unsigned>(D.fcnt), fs);
             k_fcg_dir<<<nblk((int64_t)n * nrhs), TPB, 0, s>>>((int64_t)n * nrhs, nrhs, z, po, p, fs, it == 0);
