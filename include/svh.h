@@ -134,6 +134,11 @@ int svh_get_toeplitz(const svh_handle* h, double* T);
  * -j*sign_a(k)*S_u(|k|) for S_a, with |k|_i = min(k_i, P_i - k_i) and
  * sign_a(k) = +1 for k_a <= P_a/2, -1 otherwise. */
 int svh_get_spectra(const svh_handle* h, double* S);
+/* The FP32 copy of the octant spectra on the device, which FP32 products
+ * read (same layout, float S[7][Hz][Hy][Hx]); after svh_rebuild_spectra or a
+ * product in SVH_KERNELS_TUCKER_REBUILD mode it holds the Tucker restore.
+ * Synchronises the handle's stream. */
+int svh_get_spectra32(svh_handle* h, float* S);
 
 /* Tucker representation (Eq. 10) of kernel `kernel_id`'s octant spectrum:
  * S = core x1 F1 x2 F2 x3 F3 with core[d3][d2][d1] (d1 index fastest),
@@ -308,9 +313,11 @@ int svh_matvec_noalloc(svh_handle* h, double omega, int nb, const void* x_dev, v
  * FP64 products always use variant 0. */
 #define SVH_NFFTPASS 7
 /* Device status word of the handle: bit 0 (SVH_STATUS_TMA_TIMEOUT) is set
- * when a kernel's bounded wait for a TMA copy expired (its results are then
- * invalid). clear != 0 resets it. */
+ * when a kernel's bounded wait for a TMA copy expired, bit 1
+ * (SVH_STATUS_MMA_TIMEOUT) when the Tucker restore's bounded wait for its
+ * tensor-core MMAs expired (results are then invalid). clear != 0 resets it. */
 #define SVH_STATUS_TMA_TIMEOUT 1
+#define SVH_STATUS_MMA_TIMEOUT 2
 int svh_get_device_status(svh_handle* h, int32_t* status, int clear);
 int svh_autotune(svh_handle* h, int nb, int32_t* variants, double* ms);
 int svh_set_pass_variant(svh_handle* h, int pass, int variant);

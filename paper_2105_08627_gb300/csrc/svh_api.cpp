@@ -119,7 +119,6 @@ static void free_kernels(Handle* h) {
         h->tk[u] = Tucker();
     }
     dev_free(h->d_tk_w1);
-    dev_free(h->d_tk_w2);
     dev_free(h->d_tk_probs);
     ++h->tk_version;
     h->have_kernels = false;
@@ -465,15 +464,8 @@ static void tucker_svd(const double* O, const int dims[3], double tol, Tucker& o
 }
 
 static int upload_tucker(Handle* h, int u) {
-    Tucker& t = h->tk[u];
-    std::vector<float> c32(t.core.begin(), t.core.end());
-    int rc = dev_upload(h, h->d_tk_core[u], c32.data(), c32.size() * sizeof(float));
+    const int rc = upload_tucker_device(h, u);
     if (rc) return rc;
-    for (int i = 0; i < 3; ++i) {
-        std::vector<float> f32(t.F[i].begin(), t.F[i].end());
-        rc = dev_upload(h, h->d_tk_F[u][i], f32.data(), f32.size() * sizeof(float));
-        if (rc) return rc;
-    }
     h->tucker_on[u] = true;
     ++h->tk_version;
     return SVH_OK;
@@ -738,6 +730,17 @@ int svh_get_spectra(const svh_handle* hh, double* S) {
     if (!h || !S) return SVH_ERR_ARG;
     if (!h->have_kernels) return SVH_ERR_STATE;
     std::memcpy(S, h->spec.data(), h->spec.size() * sizeof(double));
+    return SVH_OK;
+}
+
+int svh_get_spectra32(svh_handle* hh, float* S) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    HCHECK(h);
+    if (!S) return set_err(h, SVH_ERR_ARG, "svh_get_spectra32: null output");
+    if (!h->have_kernels || !h->d_spec32.p) return set_err(h, SVH_ERR_STATE, "svh_get_spectra32: no kernels");
+    SVH_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    SVH_CUDA_TRY(h, cudaMemcpy(S, h->d_spec32.p, (size_t)7 * h->Hx * h->Hy * h->Hz * sizeof(float),
+                               cudaMemcpyDeviceToHost));
     return SVH_OK;
 }
 

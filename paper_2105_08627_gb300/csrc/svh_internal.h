@@ -64,8 +64,10 @@ struct Handle {
     FftPlanHost plan[3];
     bool tucker_on[7] = {false, false, false, false, false, false, false};
     Tucker tk[7];
-    DevBuf d_tk_core[7], d_tk_F[7][3];   // float
-    DevBuf d_tk_w1, d_tk_w2;             // rebuild intermediates (float)
+    // device form of the Tucker data (float, rows padded to 8): core x_3 F3 as
+    // [Hz][d2p][d1p], F1 as [Hx][d1p], F2 as [Hy][d2p] (d_tk_F[u][2] unused)
+    DevBuf d_tk_core[7], d_tk_F[7][3];
+    DevBuf d_tk_w1;                      // restore intermediate [Hx][Hz][d2p] per kernel (float)
     DevBuf d_tk_probs;                   // GEMM descriptors of the restore
     std::vector<char> tk_probs;          // host copy of the descriptors
     int tk_probs_split[3] = {0, 0, 0};
@@ -166,6 +168,8 @@ int precond_schur_solve_dev(Handle* h, int nb, int per_freq, const void* e_dev, 
 // Tucker rebuild (tucker.cu)
 // restore the FP32 spectra from Tucker data (Eq. 10) into d_spec32
 int launch_tucker_rebuild(Handle* h, cudaStream_t s);
+// uploads the device form of h->tk[u] (tucker.cu)
+int upload_tucker_device(Handle* h, int u);
 
 }  // namespace svh
 

@@ -66,6 +66,7 @@ class svh_grid_info(C.Structure):
 
 _P = C.c_void_p
 _DP = C.POINTER(C.c_double)
+_FP = C.POINTER(C.c_float)
 _I32P = C.POINTER(C.c_int32)
 _I64P = C.POINTER(C.c_int64)
 _U8P = C.POINTER(C.c_uint8)
@@ -85,6 +86,7 @@ SIGNATURES = {
     "svh_load_toeplitz": (C.c_int, [_P, _DP]),
     "svh_get_toeplitz": (C.c_int, [_P, _DP]),
     "svh_get_spectra": (C.c_int, [_P, _DP]),
+    "svh_get_spectra32": (C.c_int, [_P, _FP]),
     "svh_load_tucker": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, _DP, _DP, _DP, _DP]),
     "svh_tucker_compress": (C.c_int, [_P, C.c_double, _I32P]),
     "svh_get_tucker": (C.c_int, [_P, C.c_int, _I32P, _DP, _DP, _DP, _DP]),
@@ -149,6 +151,10 @@ def lib():
 
 def _dp(a):
     return a.ctypes.data_as(_DP)
+
+
+def _fp(a):
+    return a.ctypes.data_as(_FP)
 
 
 def _i32p(a):
@@ -342,6 +348,13 @@ class Handle:
         i = self.info()
         S = np.empty((7, i["Hz"], i["Hy"], i["Hx"]))
         self._ck(lib().svh_get_spectra(self._h, _dp(S)), "svh_get_spectra")
+        return S
+
+    def spectra32(self):
+        """The FP32 octant spectra on the device (what FP32 products read)."""
+        i = self.info()
+        S = np.empty((7, i["Hz"], i["Hy"], i["Hx"]), np.float32)
+        self._ck(lib().svh_get_spectra32(self._h, _fp(S)), "svh_get_spectra32")
         return S
 
     def load_tucker(self, u, core, Fs):

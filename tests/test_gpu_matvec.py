@@ -186,6 +186,29 @@ def test_tucker_rebuild_matches_oracle_restore():
     h.close()
 
 
+@pytest.mark.parametrize("case", ["blob", "meander256"])
+def test_tucker_restore_elementwise(case):
+    """a1: the tensor-core restore (Eq. 10-11: modes 1 and 2 as tcgen05 GEMMs, mode 3 folded
+    into the core at load) of every FP32 spectrum value, against the oracle's FP64 restore
+    of the same Tucker data. The blob's octant (25 x 25 x 7) is one masked 128-row tile; the
+    256x256x8 meander's (257 x 257 x 9) has two full row tiles and a Nyquist row done by the
+    FP32 edge blocks; G00's low ranks end in a partial k slice."""
+    torch = _torch()
+    from oracle import tucker as tk
+    s = S.random_blob(53, 24, 20, 6, fill=0.4) if case == "blob" else S.meander_cfg2()
+    h = handle_for(s)
+    ranks = h.tucker_compress(1e-8)
+    h.rebuild_spectra()
+    got = h.spectra32().astype(np.float64)
+    for u in range(7):
+        C, Fs = h.get_tucker(u)
+        ref = np.transpose(tk.tucker_restore(np.transpose(C, (2, 1, 0)), Fs), (2, 1, 0))
+        err = np.abs(got[u] - ref).max() / np.abs(ref).max()
+        assert err <= 1e-5, (u, tuple(ranks[u]), err)
+    assert h.device_status() == 0
+    h.close()
+
+
 def test_tucker_compress_error_bound():
     torch = _torch()
     from paper_2105_08627_gb300 import svh
