@@ -38,7 +38,10 @@ namespace svh {
 
 constexpr int TC_BM = 128;       // rows of a tile = MMA M = TMEM lanes
 constexpr int TC_BK = 32;        // k per pipeline stage: one 128-byte swizzled row of FP32
-constexpr int TC_MAXN = 160;     // widest tile (three pipeline stages fit shared memory)
+#ifndef SVH_TC_MAXN
+#define SVH_TC_MAXN 160
+#endif
+constexpr int TC_MAXN = SVH_TC_MAXN;   // widest tile: 160 leaves room for three pipeline stages, 256 for two
 constexpr int TC_TMEM_COLS = 256;
 constexpr int TC_EDGE = 8;       // up to this many rows past the last full tile: FP32 rows
 constexpr int TC_THREADS = 192;  // warps 0-3 epilogue (+ edge rows), 4 TMA producer, 5 MMA issuer + TMEM
