@@ -174,10 +174,12 @@ def restore_flops(info, ranks):
     return sum(2.0 * Hx * Hz * int(r[1]) * int(r[0]) + 2.0 * Hz * Hy * Hx * int(r[1]) for r in ranks)
 
 
-def pass_bytes(info, nb, csz, fused=False):
+def pass_bytes(info, nb, csz, fused=False, zk_planes=0):
     """Algorithmic HBM bytes of each pass for one batched call (compulsory reads + writes).
     fused: the y/z/y passes run as one kernel (reported under z_pass) that reads and
-    writes only the active x-lines and reads the spectra."""
+    writes only the active x-lines and reads the spectra. zk_planes > 0: the direct z pass,
+    which reads 7 z-space kernels of zk_planes planes (FP32) instead of the octant spectra
+    (made from them after each restore: read the spectra, write the kernels)."""
     K, M = info["K"], info["M"]
     nza, nrows = info["n_active_planes"], info["n_active_rows"]
     Kx, Px, Py = info["Kx"], info["Px"], info["Py"]
@@ -195,11 +197,12 @@ def pass_bytes(info, nb, csz, fused=False):
             "x_inv_epilogue": nb * (rows_line + 5 * K * csz + 5 * K * csz + M * csz) + vidx + 40 * K,
             "node_rows": nb * (5 * K * csz + M * csz) + 9 * M,
         }
+    zk = 7 * info["Hx"] * info["Hy"] * zk_planes * 4
     return {
-        "tucker_rebuild": 7 * Ht * 4,
+        "tucker_rebuild": 7 * Ht * 4 + (7 * Ht * 4 + zk if zk_planes else 0),
         "x_fwd": nb * (5 * K * csz + rows_line) + vidx,
         "y_fwd": nb * (rows_line + planes),
-        "z_pass": nb * 2 * planes + 7 * Ht * csz // 2,
+        "z_pass": nb * 2 * planes + (zk if zk_planes else 7 * Ht * csz // 2),
         "y_inv": nb * (planes + rows_line),
         "x_inv_epilogue": nb * (rows_line + 5 * K * csz + 5 * K * csz + M * csz) + vidx + 40 * K,
         "node_rows": nb * (5 * K * csz + M * csz) + 9 * M,
@@ -473,7 +476,10 @@ def run_svh(args):
     _, (pass_ms, ncalls) = time_steps(h, torch, omega, x, y, args.steps, flush, profile=True)
     cnt, cho = h.pass_variants()
     fused = bool(cnt[5] == 2 and cho[5] == 1)
-    pb = pass_bytes(info, nb, 8, fused)
+    zdirect = not fused and int(cho[2]) == 3
+    zact = np.nonzero(s.occ.reshape(s.occ.shape[0], -1).any(axis=1))[0]
+    zspan = int(zact[-1] - zact[0] + 1) if len(zact) else 0
+    pb = pass_bytes(info, nb, 8, fused, zk_planes=zspan if zdirect else 0)
     dom = max((k for k in pass_ms if k != "tucker_rebuild"), key=lambda k: pass_ms[k])
     per_launch_ms = pass_ms[dom] / ncalls
     peak, peak_kind = peaks()
@@ -481,7 +487,7 @@ def run_svh(args):
     traffic = traffic_from_profiles(dom, args.workload)
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
-                "path": "fused y/z/y" if fused else "separate passes",
+                "path": "fused y/z/y" if fused else ("separate passes, direct z" if zdirect else "separate passes"),
                 "algorithmic_bytes_per_launch": pb[dom], "avg_launch_ms": per_launch_ms,
                 "share_of_step": pass_ms[dom] / sum(pass_ms.values()),
                 "pass_ms_per_step": {k: v / ncalls for k, v in pass_ms.items()},

@@ -51,7 +51,13 @@ struct PassArgs {
     int zcontig;             // 1 when the active planes are consecutive
     int var;                 // tile variant of the pass being launched (0: default)
     int* status;             // device status word: kernels set bits on a bounded wait that timed out
+    const float* zk;         // z-space kernels [7][zkD][Hy][Hx] of the direct z pass (FP32) or nullptr
+    int zkD;                 // their plane offsets 0 .. zkD - 1
 };
+
+// direct z pass (fast_zd.cu): up to ZD_MAX_NZA active planes spanning at most ZK_MAX_D
+// planes, octants of at most ZK_MAX_HZ z planes
+constexpr int ZD_MAX_NZA = 8, ZK_MAX_D = 16, ZK_MAX_HZ = 25;
 
 
 // outward flux of basis alpha through face f (-x,+x,-y,+y,-z,+z)
@@ -733,6 +739,8 @@ __global__ void __launch_bounds__(160) k_zpass_tma(const __grid_constant__ PassA
 template <typename T> bool launch_x_fast(const PassArgs& a, bool inv, cudaStream_t s);
 template <typename T> bool launch_y_fast(const PassArgs& a, bool inv, cudaStream_t s);
 template <typename T> bool launch_z_fast(const PassArgs& a, cudaStream_t s);
+bool launch_z_direct(const PassArgs& a, cudaStream_t s);
+void launch_spec_to_zk(const float* S, float* R, const float* W, int Hx, int Hy, int Hz, int D, cudaStream_t s);
 bool z_fast_size(int Pz);
 // number of tile variants of a pass at this size (0: no specialised kernel)
 int x_fast_variants(int Px, bool inv, bool fp32);

@@ -420,7 +420,40 @@ static PassArgs pass_args(Handle* h, double omega, const double* d_omegas, int n
     for (int i = 1; i < nza; ++i)
         if (h->zlist[i] != h->zlist[0] + i) pa.zcontig = 0;
     pa.status = static_cast<int*>(h->d_status.p);
+    pa.zk = static_cast<const float*>(h->d_zk32.p);
+    pa.zkD = h->zk_D;
     return pa;
+}
+
+// ---- direct z pass (fast_zd.cu): available for few active planes on the specialised z sizes
+static bool z_direct_ok(const Handle* h) {
+    const int nza = (int)h->zlist.size();
+    return nza >= 1 && nza <= ZD_MAX_NZA && zk_planes(h) <= ZK_MAX_D && h->Hz <= ZK_MAX_HZ &&
+           z_fast_variants(h->Pz, true) == 3;
+}
+// the z-space kernels r_u(dz), dz = 0 .. D - 1 (fast_zd.cu): buffers and weights (zk_weights)
+// for the current active planes, then, unless `alloc_only`, made from the FP32 octant spectra
+// when those changed since (or `force`)
+static int ensure_zk(Handle* h, cudaStream_t s, bool force, bool alloc_only = false) {
+    const int D = zk_planes(h), Hz = h->Hz;
+    const size_t plane = (size_t)h->Hx * h->Hy;
+    if (h->zk_D != D || !h->d_zk32.p) {
+        if (int rc = dev_alloc(h, h->d_zk32, (size_t)7 * D * plane * sizeof(float))) return rc;
+        std::vector<double> wd;
+        zk_weights(h->Pz, Hz, D, wd);
+        const std::vector<float> w(wd.begin(), wd.end());
+        if (int rc = dev_upload(h, h->d_zkw, w.data(), w.size() * sizeof(float))) return rc;
+        h->zk_D = D;
+        h->zk_version = -1;
+    }
+    if (alloc_only) return SVH_OK;
+    if (force || h->zk_version != h->spec_version) {
+        launch_spec_to_zk(static_cast<const float*>(h->d_spec32.p), static_cast<float*>(h->d_zk32.p),
+                          static_cast<const float*>(h->d_zkw.p), h->Hx, h->Hy, Hz, D, s);
+        SVH_CUDA_TRY(h, cudaGetLastError());
+        h->zk_version = h->spec_version;
+    }
+    return SVH_OK;
 }
 
 // The launch sequence on caller-provided intermediate grids B1, B2.
@@ -455,6 +488,8 @@ static int run_matvec(Handle* h, double omega, const double* d_omegas, int nb, c
     ensure_smem_optin(h);
     const bool fused = ti == 0 && h->tune32[5] == 1 && fused_path_ok(pa, h->smem_optin);
     const bool rebuild = allow_rebuild && ti == 0 && h->kernel_mode == SVH_KERNELS_TUCKER_REBUILD;
+    // the direct z pass reads the z-space kernels, made from the spectra (after the restore)
+    const bool zdirect = ti == 0 && !fused && h->tune32[2] == 3 && z_direct_ok(h);
     cudaStream_t s = h->stream, sa = nullptr;
     if (int rc = ensure_aux(h)) return rc;
     sa = h->aux;
@@ -474,7 +509,18 @@ static int run_matvec(Handle* h, double omega, const double* d_omegas, int nb, c
     cudaStream_t s_rb = sched == 0 ? sa : s, s_nd = sched == 2 ? s : sa;
     int rc_aux = SVH_OK;
     prof_at(h, 0, 0, s_rb);
-    if (rebuild) rc_aux = launch_tucker_rebuild(h, s_rb);   // pass 3 needs the spectra (Eq. 10)
+    // pass 3 needs the spectra (Eq. 10), or for the direct z pass their z-space kernels,
+    // which the restore then writes directly
+    if (rebuild && zdirect) {
+        rc_aux = ensure_zk(h, s_rb, false, true);
+        if (!rc_aux) rc_aux = launch_tucker_rebuild(h, s_rb, true);
+    } else if (rebuild) {
+        rc_aux = launch_tucker_rebuild(h, s_rb, false);
+    } else if (zdirect) {
+        rc_aux = ensure_zk(h, s_rb, false);
+    }
+    pa.zk = static_cast<const float*>(h->d_zk32.p);
+    pa.zkD = h->zk_D;
     prof_at(h, 0, 1, s_rb);
     cudaEventRecord(h->ev_spec, s_rb);
     if (preforked && s_nd == sa) cudaStreamWaitEvent(sa, h->ev_x, 0);   // the node rows read the input
@@ -536,7 +582,9 @@ static int run_matvec(Handle* h, double omega, const double* d_omegas, int nb, c
         cudaStreamWaitEvent(s, h->ev_spec, 0);
         prof_at(h, 3, 0, s);
         pa.var = var(2);
-        if (!launch_z_fast<T>(pa, s)) {
+        if (zdirect) {
+            if (!rc_aux && !launch_z_direct(pa, s)) rc_aux = set_err(h, SVH_ERR_STATE, "svh_matvec: direct z pass unavailable");
+        } else if (!launch_z_fast<T>(pa, s)) {
             int tbz = std::max(1, std::min(64, MAXPTS * NTHR / (5 * Pz)));
             size_t sm = (size_t)(Pz + Pz * 5 * tbz) * csz;
             cudaFuncSetAttribute(k_zpass<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -618,7 +666,7 @@ static int pass_variants(const Handle* h, int p, const PassArgs* pa = nullptr) {
         case 6: return 3;
         case 0: return x_fast_variants(h->Px, false, true);
         case 1: return y_fast_variants(h->Py, true);
-        case 2: return z_fast_variants(h->Pz, true);
+        case 2: return z_fast_variants(h->Pz, true) + (z_direct_ok(h) ? 1 : 0);
         case 3: return y_fast_variants(h->Py, true);
         default: return x_fast_variants(h->Px, true, true);
     }
@@ -628,7 +676,7 @@ static bool launch_pass(const PassArgs& a, int p, cudaStream_t s) {
     switch (p) {
         case 0: return launch_x_fast<float>(a, false, s);
         case 1: return launch_y_fast<float>(a, false, s);
-        case 2: return launch_z_fast<float>(a, s);
+        case 2: return a.var == 3 ? launch_z_direct(a, s) : launch_z_fast<float>(a, s);
         case 3: return launch_y_fast<float>(a, true, s);
         default: return launch_x_fast<float>(a, true, s);
     }
@@ -676,6 +724,7 @@ int autotune(Handle* h, int nb, int32_t* variants, double* ms) {
         cudaEventCreate(&e1) != cudaSuccess)
         return done(set_err(h, SVH_ERR_CUDA, "svh_autotune: CUDA set-up failed"));
     ensure_smem_optin(h);
+    if (z_direct_ok(h) && (rc = ensure_zk(h, s, false))) return done(rc);
     PassArgs pa = pass_args<float>(h, 2e9 * 3.14159265358979323846, nullptr, nb, x.p, y.p, 0, h->d_B1.p, h->d_B2.p);
     std::array<int, SVH_NTUNE> best{};
     constexpr int REPS = 5;
@@ -685,7 +734,7 @@ int autotune(Handle* h, int nb, int32_t* variants, double* ms) {
         best[p] = 0;
         for (int v = 0; v < nv; ++v) {
             pa.var = v;
-            launch_pass(pa, p, s);   // warm-up (and the shared-memory attribute)
+            if (!launch_pass(pa, p, s)) continue;   // warm-up (and the shared-memory attribute)
             cudaEventRecord(e0, s);
             for (int r = 0; r < REPS; ++r) launch_pass(pa, p, s);
             cudaEventRecord(e1, s);

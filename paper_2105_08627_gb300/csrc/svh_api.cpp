@@ -110,16 +110,22 @@ static FftPlanHost make_plan(int N) {
 
 static void free_kernels(Handle* h) {
     dev_free(h->d_spec32);
+    dev_free(h->d_zk32);
+    dev_free(h->d_zkw);
+    h->zk_D = 0;
+    h->zk_version = -1;
     dev_free(h->d_spec64);
     for (int i = 0; i < 3; ++i) { dev_free(h->d_tw32[i]); dev_free(h->d_tw64[i]); }
     for (int u = 0; u < 7; ++u) {
         dev_free(h->d_tk_core[u]);
+        dev_free(h->d_tk_core_zk[u]);
         for (int i = 0; i < 3; ++i) dev_free(h->d_tk_F[u][i]);
         h->tucker_on[u] = false;
         h->tk[u] = Tucker();
     }
     dev_free(h->d_tk_w1);
     dev_free(h->d_tk_probs);
+    h->tk_zk_D = 0;
     ++h->tk_version;
     h->have_kernels = false;
     h->toep.clear();
@@ -257,6 +263,7 @@ static int install_kernels(Handle* h) {
     if (rc) return rc;
     std::vector<float> s32(h->spec.begin(), h->spec.end());
     rc = dev_upload(h, h->d_spec32, s32.data(), 7 * Ht * sizeof(float));
+    ++h->spec_version;
     if (rc) return rc;
     const int P[3] = {h->Px, h->Py, h->Pz};
     const double twopi = 6.283185307179586476925286766559;

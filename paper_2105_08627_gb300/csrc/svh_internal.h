@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
 #include <string>
 #include <vector>
 
@@ -60,6 +61,11 @@ struct Handle {
     std::vector<double> toep;          // [7][Kz][Ky][Kx]
     std::vector<double> spec;          // [7][Hz][Hy][Hx]
     DevBuf d_spec32, d_spec64;         // float / double [7][Hz][Hy][Hx]
+    int spec_version = 0;              // bumped whenever d_spec32 is rewritten
+    // z-space kernels of the direct z pass: float [7][zk_D][Hy][Hx], made from d_spec32
+    // with the weights d_zkw [2][zk_D][Hz] (cosines, sines); current when zk_version == spec_version
+    DevBuf d_zk32, d_zkw;
+    int zk_D = 0, zk_version = -1;
     DevBuf d_tw32[3], d_tw64[3];       // twiddles per axis
     FftPlanHost plan[3];
     bool tucker_on[7] = {false, false, false, false, false, false, false};
@@ -67,6 +73,11 @@ struct Handle {
     // device form of the Tucker data (float, rows padded to 8): core x_3 F3 as
     // [Hz][d2p][d1p], F1 as [Hx][d1p], F2 as [Hy][d2p] (d_tk_F[u][2] unused)
     DevBuf d_tk_core[7], d_tk_F[7][3];
+    // core x_3 (W_u F3) for a restore straight to the z-space kernels of the direct z pass
+    // (W_u the [zk_D][Hz] weights of zk_weights), planes [2][zk_D d2p][d1p]; built for tk_zk_D planes
+    DevBuf d_tk_core_zk[7];
+    int tk_zk_D = 0;
+    int tk_probs_target = -1;            // 0: the descriptors write the spectra, 1: the z-space kernels
     DevBuf d_tk_w1;                      // restore intermediate [Hx][Hz][d2p] per kernel (float)
     DevBuf d_tk_probs;                   // GEMM descriptors of the restore
     std::vector<char> tk_probs;          // host copy of the descriptors
@@ -167,7 +178,28 @@ void amg_dev_destroy(void* d);
 int precond_schur_solve_dev(Handle* h, int nb, int per_freq, const void* e_dev, void* b_dev);
 // Tucker rebuild (tucker.cu)
 // restore the FP32 spectra from Tucker data (Eq. 10) into d_spec32
-int launch_tucker_rebuild(Handle* h, cudaStream_t s);
+// restore of the kernels with Tucker data on `s`: into the FP32 octant spectra (to_zk false,
+// bumps spec_version) or straight into the z-space kernels d_zk32 (to_zk true; needs zk_D set)
+int launch_tucker_rebuild(Handle* h, cudaStream_t s, bool to_zk = false);
+// plane span of the active planes (the z offsets the direct z pass needs: 0 .. span - 1)
+inline int zk_planes(const Handle* h) {
+    return h->zlist.empty() ? 0 : h->zlist.back() - h->zlist.front() + 1;
+}
+// weights of the z-space kernels r_u(dz) = sum_az w[dz][az] S_u(az), dz < D, az < Hz, for the
+// z-even kernels (w[0 .. D Hz)) and for S_z (w[D Hz .. 2 D Hz)): c_az cos(2 pi az dz / Pz) and
+// c_az sin(2 pi az dz / Pz), c_az = 2 inside the octant, 1 at az = 0 and az = Pz / 2 (where the
+// odd S_z spectrum vanishes, so its weight is 0)
+inline void zk_weights(int Pz, int Hz, int D, std::vector<double>& w) {
+    w.assign((size_t)2 * D * Hz, 0.0);
+    const double pi = 3.14159265358979323846;
+    for (int d = 0; d < D; ++d)
+        for (int az = 0; az < Hz; ++az) {
+            const bool edge = az == 0 || 2 * az == Pz;
+            const double th = 2.0 * pi * az * d / Pz;
+            w[(size_t)d * Hz + az] = (edge ? 1.0 : 2.0) * std::cos(th);
+            w[(size_t)(D + d) * Hz + az] = edge ? 0.0 : 2.0 * std::sin(th);
+        }
+}
 // uploads the device form of h->tk[u] (tucker.cu)
 int upload_tucker_device(Handle* h, int u);
 

@@ -69,6 +69,20 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const void* tmap, uint64_
 // cuTensorMapEncodeTiled through the runtime's driver entry point (fast_z.cu); null if unavailable
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
 
+// asynchronous global -> shared copies of 4 or 8 bytes (cp.async, L1-allocating), in commit groups
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// waits until at most N of this thread's committed groups are pending
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // ---------------------------------------------------------------- tcgen05
 // TMEM allocation (one warp, .sync.aligned): writes the base address to *slot
 __device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {

@@ -373,28 +373,54 @@ static std::vector<float> split_planes(const double* X, int rows, int K, int Kp)
     return out;
 }
 
+// core x_3 G (Eq. 11, mode 3, FP64) for a [P][d3] matrix G, rows (p, b) padded to d2p
+static std::vector<double> fold_mode3(const Tucker& t, const double* G, int P, int d2p) {
+    const int d1 = t.d[0], d2 = t.d[1], d3 = t.d[2];
+    std::vector<double> cp((size_t)P * d2p * d1, 0.0);
+    for (int p = 0; p < P; ++p)
+        for (int c = 0; c < d3; ++c) {
+            const double w = G[(size_t)p * d3 + c];
+            for (int b = 0; b < d2; ++b) {
+                const double* src = t.core.data() + ((size_t)c * d2 + b) * d1;
+                double* dst = cp.data() + ((size_t)p * d2p + b) * d1;
+                for (int a = 0; a < d1; ++a) dst[a] += w * src[a];
+            }
+        }
+    return cp;
+}
+
 int upload_tucker_device(Handle* h, int u) {
     const Tucker& t = h->tk[u];
     const int d1 = t.d[0], d2 = t.d[1], d3 = t.d[2];
     const int d1p = pad8(d1), d2p = pad8(d2);
     const int Hx = h->Hx, Hy = h->Hy, Hz = h->Hz;
-    // core' = core x_3 F3 (Eq. 11, mode 3) in FP64, rows (kz, b) with b padded to d2p
-    std::vector<double> cp((size_t)Hz * d2p * d1, 0.0);
-    for (int kz = 0; kz < Hz; ++kz)
-        for (int c = 0; c < d3; ++c) {
-            const double w = t.F[2][(size_t)kz * d3 + c];
-            for (int b = 0; b < d2; ++b) {
-                const double* src = t.core.data() + ((size_t)c * d2 + b) * d1;
-                double* dst = cp.data() + ((size_t)kz * d2p + b) * d1;
-                for (int a = 0; a < d1; ++a) dst[a] += w * src[a];
-            }
-        }
+    // core' = core x_3 F3: the restore of the octant spectra
+    const std::vector<double> cp = fold_mode3(t, t.F[2].data(), Hz, d2p);
     const std::vector<float> core_s = split_planes(cp.data(), Hz * d2p, d1, d1p);
     const std::vector<float> f1_s = split_planes(t.F[0].data(), Hx, d1, d1p);
     const std::vector<float> f2_s = split_planes(t.F[1].data(), Hy, d2, d2p);
     int rc = dev_upload(h, h->d_tk_core[u], core_s.data(), core_s.size() * sizeof(float));
     if (!rc) rc = dev_upload(h, h->d_tk_F[u][0], f1_s.data(), f1_s.size() * sizeof(float));
     if (!rc) rc = dev_upload(h, h->d_tk_F[u][1], f2_s.data(), f2_s.size() * sizeof(float));
+    // core x_3 (W_u F3): the restore straight to the z-space kernels r_u(dz), dz < D (the
+    // cosine weights for the z-even kernels, the sine weights for S_z)
+    const int D = zk_planes(h);
+    if (!rc && D >= 1 && D <= Hz) {
+        std::vector<double> w;
+        zk_weights(h->Pz, Hz, D, w);
+        const double* Wu = w.data() + (u == 3 ? (size_t)D * Hz : 0);
+        std::vector<double> G((size_t)D * d3, 0.0);
+        for (int d = 0; d < D; ++d)
+            for (int c = 0; c < d3; ++c) {
+                double acc = 0;
+                for (int az = 0; az < Hz; ++az) acc += Wu[(size_t)d * Hz + az] * t.F[2][(size_t)az * d3 + c];
+                G[(size_t)d * d3 + c] = acc;
+            }
+        const std::vector<double> cz = fold_mode3(t, G.data(), D, d2p);
+        const std::vector<float> cz_s = split_planes(cz.data(), D * d2p, d1, d1p);
+        rc = dev_upload(h, h->d_tk_core_zk[u], cz_s.data(), cz_s.size() * sizeof(float));
+        h->tk_zk_D = D;
+    }
     return rc;
 }
 
@@ -455,9 +481,14 @@ static TcStage* stages_of(Handle* h) {
     return reinterpret_cast<TcStage*>((p + 63) & ~uintptr_t(63));
 }
 
-int launch_tucker_rebuild(Handle* h, cudaStream_t strm) {
+int launch_tucker_rebuild(Handle* h, cudaStream_t strm, bool to_zk) {
     const int Hx = h->Hx, Hy = h->Hy, Hz = h->Hz;
-    const int64_t Ht = (int64_t)Hx * Hy * Hz;
+    // planes of the restored octant: Hz spectra planes, or D z-offsets of the z-space kernels
+    const int NP = to_zk ? h->zk_D : Hz;
+    if (to_zk && (NP < 1 || NP > Hz || h->tk_zk_D != NP || !h->d_zk32.p))
+        return set_err(h, SVH_ERR_STATE, "Tucker restore: no z-space form of the Tucker data for these planes");
+    float* out = static_cast<float*>(to_zk ? h->d_zk32.p : h->d_spec32.p);
+    const int64_t Ht = (int64_t)Hx * Hy * NP;
     size_t n1 = 0;
     for (int u = 0; u < 7; ++u)
         if (h->tucker_on[u]) n1 += (size_t)2 * Hz * Hx * pad8(h->tk[u].d[1]);
@@ -468,9 +499,8 @@ int launch_tucker_rebuild(Handle* h, cudaStream_t strm) {
         if (rc) return rc;
         fresh = true;
     }
-    if (fresh || h->tk_probs_version != h->tk_version) {
+    if (fresh || h->tk_probs_version != h->tk_version || h->tk_probs_target != (int)to_zk) {
         float* w1 = static_cast<float*>(h->d_tk_w1.p);
-        float* spec = static_cast<float*>(h->d_spec32.p);
         h->tk_probs.assign(2 * sizeof(TcStage) + 64, 0);   // tensor maps want 64-byte alignment
         TcStage* st = stages_of(h);
         bool ok = true;
@@ -479,16 +509,16 @@ int launch_tucker_rebuild(Handle* h, cudaStream_t strm) {
         for (int u = 0; u < 7; ++u) {
             if (!h->tucker_on[u]) continue;
             const int d1p = pad8(h->tk[u].d[0]), d2p = pad8(h->tk[u].d[1]);
-            const float* core = static_cast<const float*>(h->d_tk_core[u].p);
+            const float* core = static_cast<const float*>((to_zk ? h->d_tk_core_zk[u] : h->d_tk_core[u]).p);
             const float* F1 = static_cast<const float*>(h->d_tk_F[u][0].p);
             const float* F2 = static_cast<const float*>(h->d_tk_F[u][1].p);
             float* W1 = w1 + o1;
-            const int64_t w1_plane = (int64_t)Hz * Hx * d2p;
-            o1 += (size_t)2 * w1_plane;
+            const int64_t w1_plane = (int64_t)NP * Hx * d2p;
+            o1 += (size_t)2 * Hz * Hx * d2p;
             // stage 1: D[kx][(kz, b)] -> W1[kz][kx][b] (split: stage 2 reads it as TF32 planes)
-            add_problem(st[0], n, F1, Hx, core, Hz * d2p, d1p, W1, d2p, d2p, (int64_t)Hx * d2p, 1, w1_plane, ok);
-            // stage 2: D[ky][(kz, kx)] -> S[kz][ky][kx]
-            add_problem(st[1], n, F2, Hy, W1, Hz * Hx, d2p, spec + u * Ht, Hx, Hx, (int64_t)Hy * Hx, 1, 0, ok);
+            add_problem(st[0], n, F1, Hx, core, NP * d2p, d1p, W1, d2p, d2p, (int64_t)Hx * d2p, 1, w1_plane, ok);
+            // stage 2: D[ky][(kz, kx)] -> out[kz][ky][kx]
+            add_problem(st[1], n, F2, Hy, W1, NP * Hx, d2p, out + u * Ht, Hx, Hx, (int64_t)Hy * Hx, 1, 0, ok);
             ++n;
         }
         if (!ok) return set_err(h, SVH_ERR_CUDA, "Tucker restore: TMA descriptor encoding failed");
@@ -497,11 +527,16 @@ int launch_tucker_rebuild(Handle* h, cudaStream_t strm) {
         h->tk_probs_split[2] = 0;
         SVH_CUDA_TRY(h, cudaFuncSetAttribute(k_tc_restore, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
         h->tk_probs_version = h->tk_version;
+        h->tk_probs_target = (int)to_zk;
     }
     const TcStage* st = stages_of(h);
     launch_stage(st[0], h->tk_probs_split[0], strm);
     launch_stage(st[1], h->tk_probs_split[1], strm);
     SVH_CUDA_TRY(h, cudaGetLastError());
+    if (to_zk)
+        h->zk_version = -2;   // the z-space kernels now come from the Tucker data, not the spectra
+    else
+        ++h->spec_version;
     return SVH_OK;
 }
 

@@ -183,6 +183,45 @@ def test_tucker_rebuild_matches_oracle_restore():
         h.set_pass_variant(6, sched)
         y2 = h.matvec(om, torch.from_numpy(x.astype(np.complex64)).cuda()).cpu().numpy().astype(np.complex128)
         assert np.array_equal(y, y2), sched
+    # every z-pass variant, the direct one reading z-space kernels made from each restore
+    counts = h.pass_variants()[0]
+    assert counts[2] == 4
+    for zv in range(counts[2]):
+        h.set_pass_variant(2, zv)
+        y3 = h.matvec(om, torch.from_numpy(x.astype(np.complex64)).cuda()).cpu().numpy().astype(np.complex128)
+        _check_fp32(y3, yref)
+    h.close()
+
+
+def test_direct_z_pass_with_empty_planes():
+    """a4: the direct z pass (block-Toeplitz product over the active planes) when the active
+    planes are not consecutive (z = 2 and 5 empty: offsets up to 7 between active planes),
+    against the oracle, resident and after a Tucker restore."""
+    torch = _torch()
+    from paper_2105_08627_gb300 import svh
+    s = S.random_blob(66, 40, 24, 8, fill=0.5)
+    for z in (2, 5):
+        s.occ[z] = 0
+        s.lam[z] = 0
+        s.sigma0[z] = 0
+    g, S7, P, T = oracle_reference(s)
+    om = 2 * np.pi * 1.5e9
+    nb = 2
+    x = S.random_complex(67, (nb, g.N))
+    yref = np.stack([op.apply_K_fft(g, S7, x[b], om, P) for b in range(nb)])
+    h = handle_for(s, toeplitz=T)
+    assert h.info()["n_active_planes"] == 6
+    counts = h.pass_variants()[0]
+    assert counts[2] == 4
+    xd = torch.from_numpy(x.astype(np.complex64)).cuda()
+    for zv in range(4):
+        h.set_pass_variant(2, zv)
+        _check_fp32(h.matvec(om, xd).cpu().numpy().astype(np.complex128), yref)
+    h.tucker_compress(1e-9)
+    h.set_kernel_mode(svh.SVH_KERNELS_TUCKER_REBUILD)
+    h.set_pass_variant(2, 3)
+    _check_fp32(h.matvec(om, xd).cpu().numpy().astype(np.complex128), yref)
+    assert h.device_status() == 0
     h.close()
 
 
