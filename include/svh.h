@@ -147,10 +147,15 @@ int svh_get_spectra32(svh_handle* h, float* S);
  * in SVH_KERNELS_TUCKER_REBUILD mode) restores it on the device (Eq. 11). */
 int svh_load_tucker(svh_handle* h, int kernel_id, int d1, int d2, int d3,
                     const double* core, const double* F1, const double* F2, const double* F3);
-/* Algorithm 1 (Tucker-SVD, host) applied to the current octant spectra with
+/* Algorithm 1 (Tucker-SVD) applied to the current FP64 octant spectra with
  * truncation ||sigma_discarded|| <= tol/sqrt(3) * ||S||_F per mode; installs
- * the result as by svh_load_tucker. ranks[7*3] (may be NULL) receives d1,d2,d3. */
+ * the result as by svh_load_tucker. ranks[7*3] (may be NULL) receives d1,d2,d3.
+ * svh_tucker_compress runs on the device (FP64 Gram matrices by cuBLAS, the
+ * symmetric eigensolver of cuSOLVER, row norms and projections on the handle's
+ * stream; synchronises it); svh_tucker_compress_on(..., on_device = 0) runs the
+ * same steps on the host cores. */
 int svh_tucker_compress(svh_handle* h, double tol, int32_t* ranks);
+int svh_tucker_compress_on(svh_handle* h, double tol, int32_t* ranks, int on_device);
 /* Copy out the Tucker data of one kernel; pass NULL arrays to query d1,d2,d3. */
 int svh_get_tucker(const svh_handle* h, int kernel_id, int32_t* d, double* core,
                    double* F1, double* F2, double* F3);

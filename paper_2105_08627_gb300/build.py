@@ -71,7 +71,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
             if l.strip():
                 print(l)
     tmp = LIB + ".tmp"
-    cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-Xcompiler", "-fopenmp,-pthread", "-lgomp", "-lpthread"]
+    cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-Xcompiler", "-fopenmp,-pthread", "-lgomp", "-lpthread", "-lcublas", "-lcusolver"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

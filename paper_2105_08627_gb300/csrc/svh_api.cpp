@@ -523,6 +523,7 @@ int svh_destroy(svh_handle* hh) {
     for (cudaEvent_t e : {h->ev_fork, h->ev_spec, h->ev_done, h->ev_x})
         if (e) cudaEventDestroy(e);
     free_all(h);
+    if (h->tsvd) tsvd_free(h->tsvd);
     delete h;
     return SVH_OK;
 }
@@ -769,14 +770,26 @@ int svh_load_tucker(svh_handle* hh, int u, int d1, int d2, int d3, const double*
 }
 
 int svh_tucker_compress(svh_handle* hh, double tol, int32_t* ranks) {
+    return svh_tucker_compress_on(hh, tol, ranks, 1);
+}
+
+int svh_tucker_compress_on(svh_handle* hh, double tol, int32_t* ranks, int on_device) {
     Handle* h = reinterpret_cast<Handle*>(hh);
     HCHECK(h);
     if (!h->have_kernels) return set_err(h, SVH_ERR_STATE, "svh_tucker_compress: load kernels first");
     if (!(tol > 0) || tol >= 1) return set_err(h, SVH_ERR_ARG, "svh_tucker_compress: need 0 < tol < 1");
     const int dims[3] = {h->Hx, h->Hy, h->Hz};
     const size_t Ht = (size_t)h->Hx * h->Hy * h->Hz;
+    // the device routine takes the QR of each unfolding's transpose, which needs it tall
+    if (h->Hx > h->Hy * h->Hz || h->Hy > h->Hx * h->Hz || h->Hz > h->Hx * h->Hy) on_device = 0;
     for (int u = 0; u < 7; ++u) {
-        tucker_svd(h->spec.data() + u * Ht, dims, tol, h->tk[u]);
+        if (on_device) {
+            Tucker t;
+            if (int rc = tucker_svd_device(h, u, tol, t)) return rc;
+            h->tk[u] = t;
+        } else {
+            tucker_svd(h->spec.data() + u * Ht, dims, tol, h->tk[u]);
+        }
         int rc = upload_tucker(h, u);
         if (rc) return rc;
         if (ranks)

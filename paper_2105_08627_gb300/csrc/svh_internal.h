@@ -99,6 +99,8 @@ struct Handle {
 
     // ---- sparse preconditioner (amg.cpp), built per frequency by the solver
     void* precond = nullptr;
+    // ---- cuBLAS / cuSOLVER handles of the device Tucker-SVD (tucker_svd_dev.cu)
+    void* tsvd = nullptr;
 
     // ---- last solve (svh_get_solution)
     std::vector<double> last_x;   // [nb][N] complex interleaved
@@ -202,6 +204,9 @@ inline void zk_weights(int Pz, int Hz, int D, std::vector<double>& w) {
 }
 // uploads the device form of h->tk[u] (tucker.cu)
 int upload_tucker_device(Handle* h, int u);
+// Algorithm 1 on kernel u's FP64 octant spectra on the device (tucker_svd_dev.cu)
+int tucker_svd_device(Handle* h, int u, double tol, Tucker& out);
+void tsvd_free(void* p);
 
 }  // namespace svh
 

@@ -89,6 +89,7 @@ SIGNATURES = {
     "svh_get_spectra32": (C.c_int, [_P, _FP]),
     "svh_load_tucker": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, _DP, _DP, _DP, _DP]),
     "svh_tucker_compress": (C.c_int, [_P, C.c_double, _I32P]),
+    "svh_tucker_compress_on": (C.c_int, [_P, C.c_double, _I32P, C.c_int]),
     "svh_get_tucker": (C.c_int, [_P, C.c_int, _I32P, _DP, _DP, _DP, _DP]),
     "svh_set_kernel_mode": (C.c_int, [_P, C.c_int]),
     "svh_rebuild_spectra": (C.c_int, [_P]),
@@ -364,9 +365,10 @@ class Handle:
         self._ck(lib().svh_load_tucker(self._h, u, d1, d2, d3, _dp(core), _dp(F1), _dp(F2), _dp(F3)),
                  "svh_load_tucker")
 
-    def tucker_compress(self, tol):
+    def tucker_compress(self, tol, device=True):
+        """Algorithm 1 on the current spectra (device by default, host cores with device=False)."""
         r = np.zeros(21, np.int32)
-        self._ck(lib().svh_tucker_compress(self._h, tol, _i32p(r)), "svh_tucker_compress")
+        self._ck(lib().svh_tucker_compress_on(self._h, tol, _i32p(r), int(bool(device))), "svh_tucker_compress")
         return r.reshape(7, 3)
 
     def get_tucker(self, u):

@@ -248,6 +248,39 @@ def test_tucker_restore_elementwise(case):
     h.close()
 
 
+def _restore(C, Fs):
+    """S[z][y][x] from core[d3][d2][d1] and F1 [Hx][d1], F2 [Hy][d2], F3 [Hz][d3] (mode products)."""
+    X = np.tensordot(C, Fs[0], axes=([2], [1]))          # [d3][d2][Hx]
+    X = np.tensordot(X, Fs[1], axes=([1], [1]))          # [d3][Hx][Hy]
+    X = np.tensordot(X, Fs[2], axes=([0], [1]))          # [Hx][Hy][Hz]
+    return np.transpose(X, (2, 1, 0))
+
+
+@pytest.mark.parametrize("case", ["blob", "meander256"])
+def test_device_tucker_svd_matches_oracle(case):
+    """f1: Algorithm 1 on the device (QR of each unfolding's transpose, SVD of the triangle,
+    ranks from the residual row norms, projections) gives the oracle's ranks (SVD of the
+    unfoldings, same truncation rule) and meets ||S - restore|| <= tol ||S|| for every
+    kernel at tol 1e-4 and 1e-8, with orthonormal factors."""
+    torch = _torch()
+    from oracle import tucker as tk
+    s = S.random_blob(54, 28, 22, 5, fill=0.4) if case == "blob" else S.meander_cfg2()
+    h = handle_for(s)
+    spec = h.spectra()
+    for tol in (1e-4, 1e-8):
+        rd = h.tucker_compress(tol, device=True)
+        for u in range(7):
+            C, Fs = h.get_tucker(u)
+            assert tuple(rd[u]) == C.shape[::-1]
+            Co, _ = tk.tucker_svd(np.transpose(spec[u], (2, 1, 0)), tol)
+            assert np.abs(np.array(Co.shape) - rd[u]).max() <= 1, (tol, u, Co.shape, rd[u])   # threshold ties
+            err = np.linalg.norm(_restore(C, Fs) - spec[u]) / np.linalg.norm(spec[u])
+            assert err <= tol, (tol, u, err)
+            for i in range(3):
+                assert np.abs(Fs[i].T @ Fs[i] - np.eye(Fs[i].shape[1])).max() < 1e-10
+    h.close()
+
+
 def test_tucker_compress_error_bound():
     torch = _torch()
     from paper_2105_08627_gb300 import svh
