@@ -290,77 +290,97 @@ static int install_kernels(Handle* h) {
 }
 
 // ------------------------------------------------------------------ Tucker-SVD (Algorithm 1)
-// Symmetric eigen-decomposition by cyclic Jacobi rotations in round-robin
-// order: each round applies n/2 rotations on disjoint index pairs, which
-// commute, so they run in parallel. A (n x n, row-major) is overwritten;
-// V receives the eigenvectors as columns, w the eigenvalues.
-static void jacobi_eig(int n, std::vector<double>& A, std::vector<double>& V, std::vector<double>& w) {
-    const int m = n + (n & 1);   // even size for the tournament pairing
-    V.assign((size_t)n * n, 0.0);
-    for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
-    std::vector<int> order(m);
+// Left singular vectors of the mode unfolding X (D rows), given its transpose
+// as D columns of length m (cols[p * m + r]): Householder QR of the tall
+// matrix [cols] = Q R (rows padded with zeros to at least D), then one-sided
+// (Hestenes) Jacobi on R, R V = U Sigma, whose accumulated rotations V are
+// the right singular vectors of R, i.e. the left singular vectors of X =
+// R^T Q^T. Both steps are backward stable, so the singular values are accurate
+// to ~ eps sigma_max (a Gram matrix would carry eps ||X||^2 instead). Pairs of
+// columns are rotated in round-robin order, disjoint pairs in parallel.
+// V: row-major D x D with the vectors as columns; w: sigma^2.
+static void svd_left_vectors(std::vector<double>& cols, int m, int D, std::vector<double>& V, std::vector<double>& w) {
+    // Householder QR, column by column
+    for (int j = 0; j < D; ++j) {
+        double* x = cols.data() + (size_t)j * m;
+        double nx = 0;
+        for (int i = j; i < m; ++i) nx += x[i] * x[i];
+        nx = std::sqrt(nx);
+        if (nx == 0) continue;
+        const double alpha = x[j] > 0 ? -nx : nx;
+        std::vector<double> v(x + j, x + m);
+        v[0] -= alpha;
+        double vn2 = 0;
+        for (double e : v) vn2 += e * e;
+        if (vn2 == 0) continue;
+#pragma omp parallel for schedule(static) if (D - j > 16)
+        for (int k = j + 1; k < D; ++k) {
+            double* y = cols.data() + (size_t)k * m + j;
+            double sdot = 0;
+            for (size_t i = 0; i < v.size(); ++i) sdot += v[i] * y[i];
+            const double f = 2.0 * sdot / vn2;
+            for (size_t i = 0; i < v.size(); ++i) y[i] -= f * v[i];
+        }
+        x[j] = alpha;
+        for (int i = j + 1; i < m; ++i) x[i] = 0.0;
+    }
+    // A = R (column-major, D x D), V = I
+    std::vector<double> A((size_t)D * D, 0.0), Vc((size_t)D * D, 0.0);
+    for (int j = 0; j < D; ++j) {
+        for (int i = 0; i <= j; ++i) A[(size_t)j * D + i] = cols[(size_t)j * m + i];
+        Vc[(size_t)j * D + j] = 1.0;
+    }
+    const int mm = D + (D & 1);
+    std::vector<int> order(mm);
     std::iota(order.begin(), order.end(), 0);
-    std::vector<double> cs(m / 2), sn(m / 2);
-    std::vector<int> pp(m / 2), qq(m / 2);
-    double fro = 0;
-    for (size_t i = 0; i < (size_t)n * n; ++i) fro += A[i] * A[i];
     for (int sweep = 0; sweep < 60; ++sweep) {
-        double off = 0;
-        for (int i = 0; i < n; ++i)
-            for (int j = 0; j < n; ++j)
-                if (i != j) off += A[(size_t)i * n + j] * A[(size_t)i * n + j];
-        if (off <= 1e-30 * fro || off == 0) break;
-        for (int round = 0; round < m - 1; ++round) {
-            int np = 0;
-            for (int k = 0; k < m / 2; ++k) {
-                int p = order[k], q = order[m - 1 - k];
+        int rotated = 0;
+        for (int round = 0; round < mm - 1; ++round) {
+#pragma omp parallel for schedule(static) reduction(+ : rotated) if (D > 64)
+            for (int k = 0; k < mm / 2; ++k) {
+                int p = order[k], q = order[mm - 1 - k];
                 if (p > q) std::swap(p, q);
-                if (q >= n) continue;  // dummy partner
-                double apq = A[(size_t)p * n + q];
-                if (std::fabs(apq) < 1e-300) continue;
-                double app = A[(size_t)p * n + p], aqq = A[(size_t)q * n + q];
-                double theta = (aqq - app) / (2.0 * apq);
-                double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
-                double c = 1.0 / std::sqrt(t * t + 1.0);
-                pp[np] = p; qq[np] = q; cs[np] = c; sn[np] = t * c; ++np;
-            }
-            // columns: A <- A J (each rotation mixes columns p and q)
-#pragma omp parallel for schedule(static) if (n > 64)
-            for (int r = 0; r < n; ++r) {
-                double* row = A.data() + (size_t)r * n;
-                double* vr = V.data() + (size_t)r * n;
-                for (int k = 0; k < np; ++k) {
-                    int p = pp[k], q = qq[k];
-                    double c = cs[k], s = sn[k];
-                    double ap = row[p], aq = row[q];
-                    row[p] = c * ap - s * aq;
-                    row[q] = s * ap + c * aq;
-                    double vp = vr[p], vq = vr[q];
-                    vr[p] = c * vp - s * vq;
-                    vr[q] = s * vp + c * vq;
+                if (q >= D) continue;   // dummy partner
+                double* ap = A.data() + (size_t)p * D;
+                double* aq = A.data() + (size_t)q * D;
+                double al = 0, be = 0, ga = 0;
+                for (int i = 0; i < D; ++i) {
+                    al += ap[i] * ap[i];
+                    be += aq[i] * aq[i];
+                    ga += ap[i] * aq[i];
                 }
-            }
-            // rows: A <- J^T A
-#pragma omp parallel for schedule(static) if (n > 64)
-            for (int k = 0; k < np; ++k) {
-                int p = pp[k], q = qq[k];
-                double c = cs[k], s = sn[k];
-                double* rp = A.data() + (size_t)p * n;
-                double* rq = A.data() + (size_t)q * n;
-                for (int j = 0; j < n; ++j) {
-                    double ap = rp[j], aq = rq[j];
-                    rp[j] = c * ap - s * aq;
-                    rq[j] = s * ap + c * aq;
+                if (std::fabs(ga) <= 1e-15 * std::sqrt(al * be) || ga == 0) continue;
+                const double zeta = (be - al) / (2.0 * ga);
+                const double t = (zeta >= 0 ? 1.0 : -1.0) / (std::fabs(zeta) + std::sqrt(1.0 + zeta * zeta));
+                const double c = 1.0 / std::sqrt(1.0 + t * t), sn = c * t;
+                double* vp = Vc.data() + (size_t)p * D;
+                double* vq = Vc.data() + (size_t)q * D;
+                for (int i = 0; i < D; ++i) {
+                    const double a0 = ap[i], a1 = aq[i];
+                    ap[i] = c * a0 - sn * a1;
+                    aq[i] = sn * a0 + c * a1;
+                    const double v0 = vp[i], v1 = vq[i];
+                    vp[i] = c * v0 - sn * v1;
+                    vq[i] = sn * v0 + c * v1;
                 }
+                ++rotated;
             }
-            // rotate the tournament (keep order[0] fixed)
-            int last = order[m - 1];
-            for (int k = m - 1; k > 1; --k) order[k] = order[k - 1];
+            const int last = order[mm - 1];
+            for (int k = mm - 1; k > 1; --k) order[k] = order[k - 1];
             order[1] = last;
         }
+        if (!rotated) break;
     }
-    w.resize(n);
-    for (int i = 0; i < n; ++i) w[i] = A[(size_t)i * n + i];
+    V.assign((size_t)D * D, 0.0);
+    w.assign(D, 0.0);
+    for (int k = 0; k < D; ++k) {
+        double s2 = 0;
+        for (int i = 0; i < D; ++i) {
+            s2 += A[(size_t)k * D + i] * A[(size_t)k * D + i];
+            V[(size_t)i * D + k] = Vc[(size_t)k * D + i];
+        }
+        w[k] = s2;
+    }
 }
 
 // mode-i product with F^T (projection), tensor stored [D3][D2][D1] (mode 1 fastest)
@@ -396,27 +416,25 @@ static void tucker_svd(const double* O, const int dims[3], double tol, Tucker& o
     int cdims[3] = {dims[0], dims[1], dims[2]};
     for (int mode = 0; mode < 3; ++mode) {
         const int D = dims[mode];
-        // Gram matrix of the mode-i unfolding of the ORIGINAL tensor (Algorithm 1)
-        std::vector<double> G((size_t)D * D, 0.0);
+        // left singular vectors of the mode-i unfolding of the ORIGINAL tensor (Algorithm 1)
         const int D1 = dims[0], D2 = dims[1], D3 = dims[2];
-#pragma omp parallel for schedule(dynamic)
-        for (int p = 0; p < D; ++p)
-            for (int q = p; q < D; ++q) {
-                double s = 0;
-                if (mode == 0) {
-                    for (size_t r = 0; r < (size_t)D2 * D3; ++r) s += O[r * D1 + p] * O[r * D1 + q];
-                } else if (mode == 1) {
-                    for (int c = 0; c < D3; ++c)
-                        for (int a = 0; a < D1; ++a)
-                            s += O[((size_t)c * D2 + p) * D1 + a] * O[((size_t)c * D2 + q) * D1 + a];
-                } else {
-                    for (size_t r = 0; r < (size_t)D1 * D2; ++r) s += O[(size_t)p * D1 * D2 + r] * O[(size_t)q * D1 * D2 + r];
-                }
-                G[(size_t)p * D + q] = s;
-                G[(size_t)q * D + p] = s;
+        const size_t R = n / D;
+        const int m = (int)std::max<size_t>(R, (size_t)D);
+        std::vector<double> cols((size_t)D * m, 0.0);   // column p: the entries with index p along this mode
+#pragma omp parallel for schedule(static)
+        for (int p = 0; p < D; ++p) {
+            double* col = cols.data() + (size_t)p * m;
+            if (mode == 0) {
+                for (size_t r = 0; r < (size_t)D2 * D3; ++r) col[r] = O[r * D1 + p];
+            } else if (mode == 1) {
+                for (int c = 0; c < D3; ++c)
+                    for (int a = 0; a < D1; ++a) col[(size_t)c * D1 + a] = O[((size_t)c * D2 + p) * D1 + a];
+            } else {
+                for (size_t r = 0; r < (size_t)D1 * D2; ++r) col[r] = O[(size_t)p * D1 * D2 + r];
             }
+        }
         std::vector<double> V, w;
-        jacobi_eig(D, G, V, w);
+        svd_left_vectors(cols, m, D, V, w);
         std::vector<int> idx(D);
         std::iota(idx.begin(), idx.end(), 0);
         std::sort(idx.begin(), idx.end(), [&](int a, int b) { return w[a] > w[b]; });
