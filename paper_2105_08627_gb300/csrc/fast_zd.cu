@@ -99,7 +99,20 @@ __global__ void __launch_bounds__(32 * NZ, 4) k_zdirect(const __grid_constant__ 
             rs[6][d][lane] = qx + qy + 4.f * qz;
         }
     }
-    const int z0 = __ldg(a.zlist + zi);
+    // this plane's offsets to the others: kernel row |dz| and the sign of S_z's odd kernel
+    int roff[NZ];
+    float rsg[NZ];
+    {
+        const int z0 = __ldg(a.zlist + zi);
+#pragma unroll
+        for (int zj = 0; zj < NZ; ++zj) {
+            const int dz = z0 - __ldg(a.zlist + zj);
+            roff[zj] = (dz < 0 ? -dz : dz) * 32 + lane;
+            rsg[zj] = dz < 0 ? -1.f : 1.f;
+        }
+    }
+    const float* rsf = &rs[0][0][0];
+    constexpr int RU = ZK_MAX_D * 32;   // stride between the 7 kernel rows of rs
     for (int b = 0; b < a.nb; ++b) {
         const int cur = b % ZD_DEPTH;
         cp_async_wait<ZD_DEPTH - 2>();
@@ -108,10 +121,9 @@ __global__ void __launch_bounds__(32 * NZ, 4) k_zdirect(const __grid_constant__ 
         C Yx = make_float2(0.f, 0.f), Yy = Yx, Yz = Yx, Y2 = Yx, Y3 = Yx;
 #pragma unroll
         for (int zj = 0; zj < NZ; ++zj) {
-            const int dz = z0 - __ldg(a.zlist + zj), ad = dz < 0 ? -dz : dz;
-            const float g = rs[0][ad][lane], sx = rs[1][ad][lane], sy = rs[2][ad][lane];
-            const float rz = dz < 0 ? -rs[3][ad][lane] : rs[3][ad][lane];
-            const float qs = rs[4][ad][lane], qd = rs[5][ad][lane], q3 = rs[6][ad][lane];
+            const float* r = rsf + roff[zj];
+            const float g = r[0], sx = r[RU], sy = r[2 * RU], rz = rsg[zj] * r[3 * RU];
+            const float qs = r[4 * RU], qd = r[5 * RU], q3 = r[6 * RU];
             const C Ix = xs[cur][0][zj][lane], Iy = xs[cur][1][zj][lane], Iz = xs[cur][2][zj][lane];
             const C I2 = xs[cur][3][zj][lane], I3 = xs[cur][4][zj][lane];
             // -i (I2 + I3) sx, -i (I3 - I2) sy: (-i v) = (v.y, -v.x)
