@@ -55,9 +55,11 @@ static void run_z(const PassArgs& a, cudaStream_t s) {
     cudaFuncSetAttribute(k_zpass_fast<T, PZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     dim3 grid((a.Px + 31) / 32, a.Py);
     // variant 0: the pruned kernel when the active planes are contiguous; 1: the full
-    // one; 2: the pruned kernel with TMA-staged boxes (FP32)
+    // one; 2: the pruned kernel with TMA-staged boxes (FP32); 4: pencils split over two
+    // threads (FP32, fast_zs.cu); other choices fall back to 0 or 1
     if constexpr (std::is_same<T, float>::value) {
         if (a.var == 2 && a.zcontig && 2 * a.nza <= PZ && run_z_tma<PZ>(a, s)) return;
+        if (a.var == 4 && launch_z_split(a, s)) return;   // 3 is the direct z pass (fast_zd.cu)
     }
     if (a.var != 1 && a.zcontig && 2 * a.nza <= PZ) {
         cudaFuncSetAttribute(k_zpass_half<T, PZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

@@ -1,0 +1,116 @@
+// fast_zs.cu -- the FFT z pass with each pencil split over two threads
+// (FP32; a tile variant of pass 3 for the long z sizes, Pz = 32 and 48).
+//
+// Same arithmetic as k_zpass_half (z-FFT, 5 x 5 block product, inverse
+// z-FFT on shifted pencils whose inputs and kept outputs lie in the lower
+// half), with each length-Pz transform split in two by decimation in time:
+// with H = Pz / 2 and W = exp(-2 pi i / Pz),
+//   X[k] = E[k] + W^k O[k],  X[k + H] = E[k] - W^k O[k]     (k < H)
+// where E, O are the length-H DFTs of the even and odd samples, and for the
+// inverse, split by output parity,
+//   x[2m] = IDFT_H(Y[k] + Y[k + H])[m],  x[2m + 1] = IDFT_H((Y[k] - Y[k + H]) W^-k)[m].
+// Thread (basis, parity, column) transforms its half (pruned: the inputs and
+// the kept outputs are the first half of each length-H line); the block
+// product task for (k, column) combines E and W^k O of all 5 bases into the
+// pair X[k], X[k + H], multiplies both and writes back the sum and the
+// twiddled difference. Half the registers of the one-thread form at Pz = 48,
+// so twice the warps fit an SM.
+#include <cuda_runtime.h>
+
+#include "fastpass.cuh"
+
+namespace svh {
+
+template <int PZ>
+__global__ void __launch_bounds__(320, 2) k_zpass_split(const __grid_constant__ PassArgs a) {
+    using C = float2;
+    constexpr int H = PZ / 2, Q = H / 2, TS = 96 / PZ;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C(*buf)[2][H][32] = reinterpret_cast<C(*)[2][H][32]>(smem_raw);   // [5][parity][k][column]
+    float(*sp)[PZ][32] = reinterpret_cast<float(*)[PZ][32]>(smem_raw + sizeof(C) * 5 * 2 * H * 32);
+    const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int al = wp >> 1, par = wp & 1;
+    const int kx0 = blockIdx.x * 32, ky = blockIdx.y, kx = kx0 + lane;
+    const bool ok = kx < a.Px;
+    load_tile_spectra<float, PZ>(a, sp, kx0, ky);
+    C* B2 = static_cast<C*>(a.B2);
+    const int64_t plane = (int64_t)a.Py * a.Px;
+    const int nza = a.nza;
+    C pre[Q];
+    auto fetch = [&](int b) {
+        const int64_t base = ((int64_t)(b * 5 + al) * nza * a.Py + ky) * a.Px + kx;
+#pragma unroll
+        for (int m = 0; m < Q; ++m) {
+            const int zi = 2 * m + par;
+            C z;
+            z.x = 0;
+            z.y = 0;
+            if (ok && zi < nza) z = B2[base + zi * plane];
+            pre[m] = z;
+        }
+    };
+    fetch(0);
+    for (int b = 0; b < a.nb; ++b) {
+        {
+            C v[H];
+            reg_fft_lowin<H, false>(pre, v);
+            if (b + 1 < a.nb) fetch(b + 1);
+#pragma unroll
+            for (int k = 0; k < H; ++k) buf[al][par][k][lane] = (par && k) ? cmul(v[k], w96<C>(k * TS)) : v[k];
+        }
+        __syncthreads();
+        for (int task = threadIdx.x; task < H * 32; task += 320) {
+            const int k = task >> 5, ln = task & 31;
+            C lo[5], hi[5];
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                const C e = buf[q][0][k][ln], o = buf[q][1][k][ln];
+                lo[q] = cadd(e, o);
+                hi[q] = csub(e, o);
+            }
+            block_multiply5<float>(lo, sp[0][k][ln], sp[1][k][ln], sp[2][k][ln], sp[3][k][ln], sp[4][k][ln],
+                                   sp[5][k][ln], sp[6][k][ln]);
+            block_multiply5<float>(hi, sp[0][k + H][ln], sp[1][k + H][ln], sp[2][k + H][ln], sp[3][k + H][ln],
+                                   sp[4][k + H][ln], sp[5][k + H][ln], sp[6][k + H][ln]);
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                buf[q][0][k][ln] = cadd(lo[q], hi[q]);
+                const C d = csub(lo[q], hi[q]);
+                buf[q][1][k][ln] = k ? cmulc(d, w96<C>(k * TS)) : d;
+            }
+        }
+        __syncthreads();
+        // each thread reads back only its own (basis, parity, column) line, which it alone writes
+        // in the next item's forward step: no further barrier is needed
+        C v[H], w[Q];
+#pragma unroll
+        for (int k = 0; k < H; ++k) v[k] = buf[al][par][k][lane];
+        reg_fft_lowout<H, true>(v, w);
+        if (ok) {
+            const int64_t base = ((int64_t)(b * 5 + al) * nza * a.Py + ky) * a.Px + kx;
+#pragma unroll
+            for (int m = 0; m < Q; ++m) {
+                const int zi = 2 * m + par;
+                if (zi < nza) B2[base + zi * plane] = w[m];
+            }
+        }
+    }
+}
+
+template <int PZ>
+static void run_zsplit(const PassArgs& a, cudaStream_t s) {
+    const size_t sm = (size_t)5 * PZ * 32 * sizeof(float2) + (size_t)7 * PZ * 32 * sizeof(float);
+    cudaFuncSetAttribute(k_zpass_split<PZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_zpass_split<PZ><<<dim3((unsigned)((a.Px + 31) / 32), (unsigned)a.Py), 320, sm, s>>>(a);
+}
+
+bool z_split_ok(int Pz, int nza, int zcontig) { return (Pz == 32 || Pz == 48) && zcontig && 2 * nza <= Pz; }
+
+bool launch_z_split(const PassArgs& a, cudaStream_t s) {
+    if (!z_split_ok(a.Pz, a.nza, a.zcontig)) return false;
+    if (a.Pz == 32) run_zsplit<32>(a, s);
+    else run_zsplit<48>(a, s);
+    return true;
+}
+
+}  // namespace svh

@@ -740,6 +740,10 @@ template <typename T> bool launch_x_fast(const PassArgs& a, bool inv, cudaStream
 template <typename T> bool launch_y_fast(const PassArgs& a, bool inv, cudaStream_t s);
 template <typename T> bool launch_z_fast(const PassArgs& a, cudaStream_t s);
 bool launch_z_direct(const PassArgs& a, cudaStream_t s);
+// z pass with each pencil split over two threads (fast_zs.cu), FP32, Pz = 32 or 48 with the active
+// planes consecutive and in the lower half
+bool z_split_ok(int Pz, int nza, int zcontig);
+bool launch_z_split(const PassArgs& a, cudaStream_t s);
 void launch_spec_to_zk(const float* S, float* R, const float* W, int Hx, int Hy, int Hz, int D, cudaStream_t s);
 bool z_fast_size(int Pz);
 // number of tile variants of a pass at this size (0: no specialised kernel)

@@ -359,6 +359,8 @@ def test_esfq_512x512x24_sampled_rows():
     (62, (48, 24, 12), False),    # P = 96, 48, 24: x inverse without a grouped kernel
     (63, (64, 64, 8), True),      # P = 128, 128, 16: the fused y/z/y path applies
     (64, (128, 128, 4), True),    # P = 256, 256, 8
+    (65, (32, 16, 16), False),    # P = 64, 32, 32: the z pass with pencils split over two threads
+    (66, (24, 16, 24), False),    # P = 48, 32, 48: the same at Pz = 48
 ])
 def test_every_tile_variant_and_autotune(seed, shape, fused):
     """a12: each FFT tile variant and path the autotuner may pick gives the oracle's product."""
