@@ -361,7 +361,14 @@ __global__ void __launch_bounds__(NT) k_ycol_fast(const __grid_constant__ PassAr
     const int zi = blockIdx.y;
     const int64_t ba = blockIdx.z;
     const int Px = a.Px;
-    const uint8_t* rm = a.rowmask + (int64_t)zi * a.Ky;
+    // the plane's row mask (rows y < Ky <= N / 2 holding voxels), staged once so that the
+    // predicated loads and stores below do not wait on a global byte load each
+    __shared__ uint8_t rm[N / 2];
+    {
+        const uint8_t* rmg = a.rowmask + (int64_t)zi * a.Ky;
+        for (int i = threadIdx.x; i < N / 2; i += NT) rm[i] = i < a.Ky ? rmg[i] : 0;
+    }
+    __syncthreads();
     {
         const int c = threadIdx.x % TB, n2 = threadIdx.x / TB;
         const bool colok = kx0 + c < Px;
