@@ -497,7 +497,7 @@ def run_svh(args):
     rf = restore_flops(info, ranks)
     t_rb = pass_ms["tucker_rebuild"] / ncalls
     tpk, tpk_kind = tensor_peak_tf32()
-    roofline["restore"] = {"bound": "tensor", "kernel": "k_tc_gemm3 (2 launches)", "unit": "TFLOP/s",
+    roofline["restore"] = {"bound": "tensor", "kernel": "k_tc_restore (2 launches)", "unit": "TFLOP/s",
                            "algorithmic_fp32_flops": rf, "tf32_mma_flops": 3 * rf, "avg_ms": t_rb,
                            "achieved": 3 * rf / (t_rb / 1e3) / 1e12, "peak": tpk, "peak_source": tpk_kind,
                            "frac": 3 * rf / (t_rb / 1e3) / 1e12 / tpk}
