@@ -134,10 +134,13 @@ int svh_get_toeplitz(const svh_handle* h, double* T);
  * -j*sign_a(k)*S_u(|k|) for S_a, with |k|_i = min(k_i, P_i - k_i) and
  * sign_a(k) = +1 for k_a <= P_a/2, -1 otherwise. */
 int svh_get_spectra(const svh_handle* h, double* S);
-/* The FP32 copy of the octant spectra on the device, which FP32 products
- * read (same layout, float S[7][Hz][Hy][Hx]); after svh_rebuild_spectra or a
- * product in SVH_KERNELS_TUCKER_REBUILD mode it holds the Tucker restore.
- * Synchronises the handle's stream. */
+/* The FP32 copy of the octant spectra on the device, which the FFT forms of
+ * the FP32 z pass read (same layout, float S[7][Hz][Hy][Hx]; S host memory,
+ * 7 Hz Hy Hx floats, owned by the caller). After svh_rebuild_spectra, or a
+ * product in SVH_KERNELS_TUCKER_REBUILD mode with an FFT z pass, it holds the
+ * Tucker restore (a rebuild-mode product with the direct z pass restores its
+ * z-space kernels instead and leaves these as they were). Synchronises the
+ * handle's stream. SVH_ERR_ARG for a null S, SVH_ERR_STATE without kernels. */
 int svh_get_spectra32(svh_handle* h, float* S);
 
 /* Tucker representation (Eq. 10) of kernel `kernel_id`'s octant spectrum:
@@ -150,10 +153,14 @@ int svh_load_tucker(svh_handle* h, int kernel_id, int d1, int d2, int d3,
 /* Algorithm 1 (Tucker-SVD) applied to the current FP64 octant spectra with
  * truncation ||sigma_discarded|| <= tol/sqrt(3) * ||S||_F per mode; installs
  * the result as by svh_load_tucker. ranks[7*3] (may be NULL) receives d1,d2,d3.
- * svh_tucker_compress runs on the device (FP64 Gram matrices by cuBLAS, the
- * symmetric eigensolver of cuSOLVER, row norms and projections on the handle's
- * stream; synchronises it); svh_tucker_compress_on(..., on_device = 0) runs the
- * same steps on the host cores. */
+ * Per mode the left singular vectors of the unfolding come from a Householder
+ * QR of its transpose and an SVD of the triangle (accurate to eps sigma_max,
+ * so the ranks are those of an SVD of the unfolding also at tol 1e-8), the
+ * rank from the residual rows u_r^T S_(i). svh_tucker_compress runs on the
+ * device (cuSOLVER QR and SVD, cuBLAS GEMMs, the library's row-norm kernels, on
+ * the handle's stream; synchronises it); svh_tucker_compress_on(..., 0) runs
+ * the same steps on the host cores (one-sided Jacobi for the SVD). Errors:
+ * SVH_ERR_STATE without kernels, SVH_ERR_ARG unless 0 < tol < 1. */
 int svh_tucker_compress(svh_handle* h, double tol, int32_t* ranks);
 int svh_tucker_compress_on(svh_handle* h, double tol, int32_t* ranks, int on_device);
 /* Copy out the Tucker data of one kernel; pass NULL arrays to query d1,d2,d3. */
