@@ -398,8 +398,10 @@ int svh_load_toeplitz_store(svh_handle* h, const char* path);
  * smallest d_i whose discarded singular values have 2-norm <= tol/sqrt(3) *
  * ||O||_F, so ||O - restore||_F <= tol ||O||_F. Outputs (caller-allocated,
  * worst-case sizes): d[3]; core[d3][d2][d1] (<= D1*D2*D3); F1[D1][d1] (<= D1*D1),
- * F2[D2][d2], F3[D3][d3]. Singular values come from the eigenvalues of the
- * unfoldings' Gram matrices (cyclic Jacobi). */
+ * F2[D2][d2], F3[D3][d3]. The singular vectors of each unfolding come from a
+ * Householder QR of its transpose and a one-sided Jacobi SVD of the triangle
+ * (host cores, OpenMP); SVH_ERR_ARG for null arrays, non-positive sizes or
+ * tol <= 0. */
 int svh_host_tucker_svd(const double* O, int D1, int D2, int D3, double tol, int32_t* d, double* core,
                         double* F1, double* F2, double* F3);
 
