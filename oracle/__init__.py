@@ -10,7 +10,8 @@ Everything here is plain, slow and in float64 / complex128:
 * ``twofluid``  -- two-fluid conductivity (Eq. 3) and the diagonal terms (Eq. 9, 16-18, 22-23)
 * ``greens``    -- unit Green's-function Toeplitz kernels over voxel pairs (Eq. 19-21, App. B)
 * ``geometry``  -- voxel list, face-node numbering, incidence matrix A (Eq. 7), ports
-* ``operator``  -- dense Z (Eq. 8), circulant embedding + FFT matvec (Eq. 9), full Eq. 7 operator
+* ``operator``  -- dense Z (Eq. 8), circulant embedding + FFT matvec (Eq. 9), full Eq. 7 operator,
+                   selected rows of the product by direct summation
 * ``tucker``    -- Tucker-SVD (Algorithm 1) and the restore by mode products (Eq. 10-11)
 * ``solve``     -- right-preconditioned GMRES(50) (Sec. III), the Schur-complement
                    preconditioner (Eq. 12-15, exact sparse solve), port admittance -> inductance

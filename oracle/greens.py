@@ -171,11 +171,27 @@ def toeplitz_signed(Kx, Ky, Kz, n_duffy=16):
     return _toeplitz_from_offsets(D, n_duffy).reshape(7, 2 * Kz - 1, 2 * Ky - 1, 2 * Kx - 1)
 
 
-def toeplitz_octant(Kx, Ky, Kz, n_duffy=16):
-    """The 7 kernels at non-negative offsets 0 <= d < K -> [7, Kz, Ky, Kx]."""
+def toeplitz_octant(Kx, Ky, Kz, n_duffy=16, processes=1):
+    """The 7 kernels at non-negative offsets 0 <= d < K -> [7, Kz, Ky, Kx].
+
+    processes > 1 integrates the z planes in that many worker processes
+    (spawned, so it is safe in a process that already uses a GPU). Every
+    offset is integrated on its own, so the result is the same to the bit."""
+    if processes > 1 and Kz > 1:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(min(processes, Kz)) as pool:
+            planes = pool.starmap(_octant_plane, [(Kx, Ky, z, n_duffy) for z in range(Kz)])
+        return np.stack(planes, axis=1)
     dz, dy, dx = np.meshgrid(np.arange(Kz), np.arange(Ky), np.arange(Kx), indexing="ij")
     D = np.stack([dx.ravel(), dy.ravel(), dz.ravel()], -1).astype(float)
     return _toeplitz_from_offsets(D, n_duffy).reshape(7, Kz, Ky, Kx)
+
+
+def _octant_plane(Kx, Ky, z, n_duffy):
+    """The 7 kernels at the offsets (0 <= dx < Kx, 0 <= dy < Ky, dz = z) -> [7, Ky, Kx]."""
+    dy, dx = np.meshgrid(np.arange(Ky), np.arange(Kx), indexing="ij")
+    D = np.stack([dx.ravel(), dy.ravel(), np.full(dx.size, z)], -1).astype(float)
+    return _toeplitz_from_offsets(D, n_duffy).reshape(7, Ky, Kx)
 
 
 def signed_from_octant(T):

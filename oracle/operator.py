@@ -123,8 +123,11 @@ def block_spectra(S7):
     return np.tensordot(BLOCKS, S7, axes=(2, 0))
 
 
-def apply_Z_fft(grid, S7, I, omega, P, mu=twofluid.MU0, workers=-1):
-    """Z @ I via Eq. 9 (I: [5K] or [5, K] complex) -> [5, K]."""
+def apply_Z_fft(grid, S7, I, omega, P, mu=twofluid.MU0, workers=-1, Zh=None):
+    """Z @ I via Eq. 9 (I: [5K] or [5, K] complex) -> [5, K].
+
+    Zh: the block spectra block_spectra(S7), when the caller has formed them
+    already (they depend on the kernels only); None forms them here."""
     K = grid.K
     I = np.asarray(I, complex).reshape(5, K)
     Px, Py, Pz = P
@@ -132,20 +135,22 @@ def apply_Z_fft(grid, S7, I, omega, P, mu=twofluid.MU0, workers=-1):
     x, y, z = grid.pos[:, 0], grid.pos[:, 1], grid.pos[:, 2]
     grids[:, z, y, x] = I
     Ihat = sfft.fftn(grids, axes=(1, 2, 3), workers=workers)
-    Zh = block_spectra(S7)
+    if Zh is None:
+        Zh = block_spectra(S7)
     Yhat = np.einsum("bapqr,apqr->bpqr", Zh, Ihat)
     Y = sfft.ifftn(Yhat, axes=(1, 2, 3), workers=workers)[:, z, y, x]
     zd = twofluid.zdiag(omega, grid.lam, grid.sigma0, grid.dx, mu)
     return zd * I + 1j * omega * mu * grid.dx * Y
 
 
-def apply_K_fft(grid, S7, xvec, omega, P, mu=twofluid.MU0, workers=-1):
-    """Eq. 7 operator on x = [I (5K); Phi (M)] using the FFT product for Z."""
+def apply_K_fft(grid, S7, xvec, omega, P, mu=twofluid.MU0, workers=-1, Zh=None):
+    """Eq. 7 operator on x = [I (5K); Phi (M)] using the FFT product for Z
+    (Zh: optional pre-formed block spectra, as in apply_Z_fft)."""
     K, M = grid.K, grid.M
     xvec = np.asarray(xvec, complex)
     I = xvec[:5 * K]
     Phi = xvec[5 * K:]
-    top = apply_Z_fft(grid, S7, I, omega, P, mu, workers).ravel() - grid.A.T @ Phi
+    top = apply_Z_fft(grid, S7, I, omega, P, mu, workers, Zh).ravel() - grid.A.T @ Phi
     bot = grid.A @ I
     return np.concatenate([top, bot])
 
@@ -180,4 +185,46 @@ def direct_rows(grid, x, omega, vox_rows, node_rows, mu=twofluid.MU0):
     for b in range(5):
         out[b] -= AT[b * K + vox_rows] @ Phi
     nodes = grid.A.tocsr()[np.asarray(node_rows)] @ x[:5 * K]
+    return out, nodes
+
+
+def direct_rows_table(grid, T, x, omega, vox_rows, node_rows, mu=twofluid.MU0):
+    """Selected rows of the Eq. 7 product by direct summation over every voxel,
+    with the unit kernels taken from a table instead of integrated per pair.
+
+    T: the kernels at the non-negative offsets, [7, Kz, Ky, Kx]
+    (greens.toeplitz_octant); a signed offset d reads T at |d|, negated for
+    S_a when d_a < 0 (S_a is odd along a, every other kernel even). x: [N]
+    or [nb, N]. Returns ([nb, 5, len(vox_rows)], [nb, len(node_rows)]) for a
+    2-D x, else the shapes of direct_rows. The cost is O(rows * K), so dense
+    inputs stay cheap at any grid size."""
+    K = grid.K
+    x = np.asarray(x, complex)
+    one = x.ndim == 1
+    X = np.atleast_2d(x)
+    nb = X.shape[0]
+    I = X[:, :5 * K].reshape(nb, 5, K)
+    Phi = X[:, 5 * K:]
+    vox_rows = np.asarray(vox_rows)
+    out = np.zeros((nb, 5, vox_rows.size), complex)
+    scale = 1j * omega * mu * grid.dx
+    for i, l in enumerate(vox_rows):
+        d = grid.pos[l][None, :] - grid.pos                        # obs - src, [K, 3]
+        a = np.abs(d)
+        Tl = T[:, a[:, 2], a[:, 1], a[:, 0]]                         # [7, K]
+        for u, ax in ((1, 0), (2, 1), (3, 2)):                       # S_x, S_y, S_z
+            Tl[u] = np.where(d[:, ax] < 0, -Tl[u], Tl[u])
+        for b in range(5):
+            for al in range(5):
+                coef = BLOCKS[b, al]
+                if coef.any():
+                    out[:, b, i] += scale * (I[:, al, :] @ (coef @ Tl))
+    zd = twofluid.zdiag(omega, grid.lam[vox_rows], grid.sigma0[vox_rows], grid.dx, mu)   # [5, rows]
+    out += zd[None] * I[:, :, vox_rows]
+    AT = grid.A.T.tocsr()
+    for b in range(5):
+        out[:, b, :] -= (AT[b * K + vox_rows] @ Phi.T).T
+    nodes = (grid.A.tocsr()[np.asarray(node_rows)] @ X[:, :5 * K].T).T
+    if one:
+        return out[0], nodes[0]
     return out, nodes

@@ -321,3 +321,48 @@ def test_direct_rows_equal_dense_product(strip):
     for b in range(5):
         assert np.allclose(yv[b], y[b * g.K + rows], rtol=1e-12, atol=1e-12 * np.abs(y).max())
     assert np.allclose(yn, y[5 * g.K + nodes], rtol=1e-12, atol=1e-12 * np.abs(y).max())
+
+
+def test_direct_rows_table_equals_dense_product():
+    """The table-driven direct rows (kernels looked up at |d| with the parity of S_a) agree with
+    the dense product, whose kernels are integrated at every signed offset, for a dense
+    multi-item input on a ragged blob (odd kernels change sign across every axis)."""
+    s = S.random_blob(31, 9, 7, 5, fill=0.6)
+    g = G.build_grid(s)
+    Ts = gr.toeplitz_signed(g.Kx, g.Ky, g.Kz)
+    To = gr.toeplitz_octant(g.Kx, g.Ky, g.Kz)
+    om = 2 * np.pi * 3e9
+    x = S.random_complex(32, (3, g.N))
+    Kd = op.dense_K(g, Ts, om)
+    y = x @ Kd.T
+    rng = np.random.default_rng(33)
+    rows = rng.choice(g.K, 20, replace=False)
+    nodes = rng.choice(g.M, 20, replace=False)
+    yv, yn = op.direct_rows_table(g, To, x, om, rows, nodes)
+    for b in range(3):
+        scale = np.abs(y[b]).max()
+        for be in range(5):
+            assert np.allclose(yv[b, be], y[b, be * g.K + rows], rtol=0, atol=1e-12 * scale)
+        assert np.allclose(yn[b], y[b, 5 * g.K + nodes], rtol=0, atol=1e-12 * scale)
+    # a 1-D x gives the shapes of direct_rows, and both direct forms agree
+    v1, n1 = op.direct_rows_table(g, To, x[1], om, rows[:5], nodes[:5])
+    v2, n2 = op.direct_rows(g, x[1], om, rows[:5], nodes[:5])
+    assert v1.shape == v2.shape == (5, 5) and np.allclose(v1, v2, rtol=0, atol=1e-12 * np.abs(v2).max())
+    assert np.allclose(n1, n2, rtol=0, atol=1e-12 * np.abs(n2).max())
+
+
+def test_toeplitz_octant_in_worker_processes_is_bit_identical():
+    a = gr.toeplitz_octant(7, 5, 4)
+    b = gr.toeplitz_octant(7, 5, 4, processes=2)
+    assert np.array_equal(a, b)
+
+
+def test_preformed_block_spectra_give_the_same_product(strip):
+    s, g, T = strip
+    P = (op.fft_size(g.Kx), op.fft_size(g.Ky), op.fft_size(g.Kz))
+    S7 = op.spectra(T, P)
+    x = S.random_complex(34, g.N)
+    om = 2 * np.pi * 1e9
+    a = op.apply_K_fft(g, S7, x, om, P)
+    b = op.apply_K_fft(g, S7, x, om, P, Zh=op.block_spectra(S7))
+    assert np.array_equal(a, b)
