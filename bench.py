@@ -1,10 +1,11 @@
 #!/usr/bin/env python
 """Throughput of the Tucker-FFT VIE operator product (Eq. 7-11) on GB300.
 
-One step = one batched operator product y = Kop x over nb right-hand sides
-(frequencies / ports) of the 256 x 256 x 8 thin-film meander over a ground
-plane with holes (seeded synthetic structure shaped like the paper's
-thin-film inductors): the Tucker restore of the kernel spectra (Eq. 10),
+One step = one batched operator product y = Kop x over nb = 16 right-hand
+sides (ports) of the 512 x 512 x 24 eSFQ-like multilayer block (seeded
+synthetic structure shaped like the paper's eSFQ subsystem, Sec. III.C: four
+metal layers, wiring, vias and a perforated ground plane, 0.5 um voxels,
+P = 1024 x 1024 x 48): the Tucker restore of the kernel spectra (Eq. 10),
 the zero-padded forward 3-D FFT of the five basis grids, the 5 x 5 block
 multiply, the inverse FFT with truncation (Eq. 9), the two-fluid diagonal
 (Eq. 3, 22-23) and the incidence A / A^T apply (Eq. 7). FP32 complex is the
@@ -16,7 +17,13 @@ by CUDA events on the library's stream.
 
 --impl reference times the CPU FP64 oracle (scipy.fft) on the same workload
 (one right-hand side per step) on the host cores; it is the only arm that
-runs the oracle besides the cpu_baseline block.
+runs the oracle besides the cpu_baseline block. The oracle's set-up (its
+quadrature of the unit kernels, their circulant spectra and the 5 x 5 block
+spectra, all independent of the right-hand side) runs once, untimed.
+
+The whole-solve block times port solves of the 256 x 256 x 8 meander (by
+default; --solve-workload) with the spectra resident and with the Tucker
+restore in every product (Sec. II.B.2).
 
 Multi-GPU (torchrun): replicas only -- every rank runs its own batch (weak
 scaling); the ranks only exchange their timings.
@@ -46,13 +53,16 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="svh", choices=["svh", "reference"])
-    p.add_argument("--nb", type=int, default=4, help="right-hand sides per step")
-    p.add_argument("--workload", default="meander256", choices=["meander256", "esfq512", "pair128", "strip16"])
+    p.add_argument("--nb", type=int, default=None,
+                   help="right-hand sides per step (default: 16 for esfq512, 4 meander256, 2 pair128, 1 strip16)")
+    p.add_argument("--workload", default="esfq512", choices=["meander256", "esfq512", "pair128", "strip16"])
+    p.add_argument("--solve-workload", default="meander256",
+                   choices=["meander256", "esfq512", "pair128", "strip16", "none"],
+                   help="structure of the whole-solve timing block (none: skip it)")
     p.add_argument("--tucker-tol", type=float, default=1e-8)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
-    p.add_argument("--no-solve", action="store_true", help="skip the whole-solve timing block")
     p.add_argument("--tiles", default=None,
                    help="comma-separated FFT tile choices (7 values, as svh_autotune reports) "
                         "instead of running the autotuner (e.g. for profiling)")
@@ -60,7 +70,10 @@ def parse():
                    help="add CR / CO of the Tucker-compressed spectra vs tolerance on plates and cubes")
     p.add_argument("--with-batch", action="store_true",
                    help="also time a graph-captured batched product over the 64 cfg-3 structures")
-    return p.parse_args()
+    a = p.parse_args()
+    if a.nb is None:
+        a.nb = {"esfq512": 16, "meander256": 4, "pair128": 2, "strip16": 1}[a.workload]
+    return a
 
 
 def structure(name):
@@ -253,30 +266,43 @@ def traffic_from_profiles(kernel, workload):
     return float(v) if v else None
 
 
-def cpu_baseline(s, nb_cap=None, min_s=10.0, max_s=30.0):
-    """The oracle's FP64 FFT product timed on the host cores (bounded sample)."""
-    import svh_synth as S
+def oracle_setup(s):
+    """The oracle's right-hand-side-independent set-up for a structure: grid, FFT sizes,
+    the 7 circulant spectra and the 5 x 5 block spectra (kernels by the oracle's own
+    quadrature, its z planes in worker processes)."""
     from oracle import geometry as G
     from oracle import greens as gr
     from oracle import operator as op
     g = G.build_grid(s)
     P = (op.fft_size(g.Kx), op.fft_size(g.Ky), op.fft_size(g.Kz))
-    T = gr.toeplitz_octant(g.Kx, g.Ky, g.Kz)
+    T = gr.toeplitz_octant(g.Kx, g.Ky, g.Kz, processes=os.cpu_count() or 1)
     S7 = op.spectra(gr.signed_from_octant(T), P)
+    Zh = op.block_spectra(S7)
+    return g, P, S7, Zh
+
+
+def cpu_baseline(s, min_s=10.0, max_s=30.0):
+    """The oracle's FP64 FFT product timed on the host cores (bounded sample)."""
+    import svh_synth as S
+    from oracle import operator as op
+    t0 = time.perf_counter()
+    g, P, S7, Zh = oracle_setup(s)
+    t_setup = time.perf_counter() - t0
     cores = os.cpu_count()
     x = S.random_complex(7, g.N)
     om = 2 * np.pi * s.freqs[0]
-    op.apply_K_fft(g, S7, x, om, P, workers=cores)     # warm-up
+    op.apply_K_fft(g, S7, x, om, P, workers=cores, Zh=Zh)     # warm-up
     n, t0 = 0, time.perf_counter()
     while True:
-        op.apply_K_fft(g, S7, x, om, P, workers=cores)
+        op.apply_K_fft(g, S7, x, om, P, workers=cores, Zh=Zh)
         n += 1
         el = time.perf_counter() - t0
         if el >= min_s or el + el / n > max_s:
             break
     return {"value": g.Kx * g.Ky * g.Kz * n / el, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{n} single-vector FP64 products of the same structure (oracle: numpy + "
-                      f"scipy.fft workers={cores}), {el:.1f} s; kernel setup untimed"}
+                      f"scipy.fft workers={cores}), {el:.1f} s; oracle set-up (kernel quadrature, "
+                      f"circulant and block spectra) {t_setup:.0f} s untimed"}
 
 
 def run_reference(args):
@@ -284,26 +310,25 @@ def run_reference(args):
     if rank != 0:
         return 0
     import svh_synth as S
-    from oracle import geometry as G
-    from oracle import greens as gr
     from oracle import operator as op
     s, desc = structure(args.workload)
-    g = G.build_grid(s)
-    P = (op.fft_size(g.Kx), op.fft_size(g.Ky), op.fft_size(g.Kz))
-    S7 = op.spectra(gr.signed_from_octant(gr.toeplitz_octant(g.Kx, g.Ky, g.Kz)), P)
+    t0 = time.perf_counter()
+    g, P, S7, Zh = oracle_setup(s)
+    t_setup = time.perf_counter() - t0
     cores = os.cpu_count()
     x = S.random_complex(7, g.N)
     om = 2 * np.pi * s.freqs[0]
     for _ in range(args.warmup):
-        op.apply_K_fft(g, S7, x, om, P, workers=cores)
+        op.apply_K_fft(g, S7, x, om, P, workers=cores, Zh=Zh)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        op.apply_K_fft(g, S7, x, om, P, workers=cores)
+        op.apply_K_fft(g, S7, x, om, P, workers=cores, Zh=Zh)
     el = time.perf_counter() - t0
     Kt = g.Kx * g.Ky * g.Kz
     val = Kt * args.steps / el
     sample = (f"{args.steps} single-vector FP64 products (oracle: numpy + scipy.fft workers={cores}); "
-              f"one right-hand side per step instead of {args.nb}")
+              f"one right-hand side per step instead of {args.nb}; oracle set-up (kernel quadrature, "
+              f"circulant and block spectra) {t_setup:.0f} s untimed")
     out = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128 (fp64 complex)",
@@ -431,6 +456,36 @@ def run_tucker_sweep(torch, svh, S):
     return out
 
 
+def run_solves(torch, svh, args, h_main, s_main, desc_main):
+    if args.solve_workload == args.workload:
+        hs, s, desc, own = h_main, s_main, desc_main, False
+    else:
+        s, desc = structure(args.solve_workload)
+        hs = svh.Handle(h_main.device, torch.cuda.current_stream().cuda_stream)
+        hs.setup_structure(s)
+        hs.generate_toeplitz()
+        hs.tucker_compress(args.tucker_tol)
+        own = True
+    out = {"workload": desc, "note": "GMRES(50), FP32 products in FP64 refinement (RRE 1e-8), "
+                                      "Schur solves by AMG-CG on the device (1e-8)"}
+    for mode, name in ((svh.SVH_KERNELS_RESIDENT, "resident"), (svh.SVH_KERNELS_TUCKER_REBUILD, "tucker_restore")):
+        hs.set_kernel_mode(mode)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = hs.solve([s.freqs[0]])
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        st = res["stats"]
+        out[name] = {"seconds": wall, "setup_s": st["setup_seconds"], "iterations": st["iterations"],
+                     "refinements": st["refinements"], "final_rre": st["final_rre"],
+                     "amg_avg_cg_iterations": st["amg_avg_iterations"],
+                     "L_pH": float(res["L"][0, 0, 0] * 1e12)}
+    hs.set_kernel_mode(svh.SVH_KERNELS_TUCKER_REBUILD)
+    if own:
+        hs.close()
+    return out
+
+
 def run_svh(args):
     ws, rank, local = dist()
     import torch
@@ -540,21 +595,11 @@ def run_svh(args):
         e2e = {"value": ws * nb * Kt * args.steps / el, "unit": UNIT,
                "h2d_bytes_per_step": nb * N * 8, "d2h_bytes_per_step": nb * N * 8,
                "entry_point": "svh_matvec_host (pinned host buffers)"}
-    # whole port solve of the same structure (FP32 products inside FP64 refinement, RRE 1e-8)
+    # whole port solves (FP32 products inside FP64 refinement, RRE 1e-8) of the solve structure,
+    # with the spectra resident and with the Tucker restore in every product (Sec. II.B.2)
     solve = None
-    if not args.no_solve:
-        torch.cuda.synchronize()
-        h.set_kernel_mode(svh.SVH_KERNELS_RESIDENT)
-        t0 = time.perf_counter()
-        res = h.solve([s.freqs[0]])
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - t0
-        st = res["stats"]
-        solve = {"seconds": wall, "setup_s": st["setup_seconds"], "iterations": st["iterations"],
-                 "refinements": st["refinements"], "final_rre": st["final_rre"],
-                 "amg_avg_cg_iterations": st["amg_avg_iterations"], "L_pH": float(res["L"][0, 0, 0] * 1e12),
-                 "note": "GMRES(50), FP32 products in FP64 refinement, Schur solves by AMG-CG on the device (1e-8)"}
-        h.set_kernel_mode(svh.SVH_KERNELS_TUCKER_REBUILD)
+    if args.solve_workload != "none":
+        solve = run_solves(torch, svh, args, h, s, desc)
     sweep = None
     if args.with_tucker_sweep and rank == 0:
         sweep = run_tucker_sweep(torch, svh, S)

@@ -229,11 +229,14 @@ typedef struct {
 
 void svh_default_options(svh_options* opt);
 /* omegas[nfreq] (rad/s, > 0); Zport receives nfreq * nports * nports complex
- * values (interleaved), Zport[f][p][q]. opt may be NULL (defaults), st may be
- * NULL. Returns SVH_ERR_NOT_CONVERGED (with Zport filled) if some residual
- * stays above rre. Requires kernels and at least one port. */
+ * values (interleaved), Zport[f][p][q]; Lport (may be NULL) receives the port
+ * inductances nfreq * nports * nports doubles, Lport[f][p][q] =
+ * Im(Zport[f][p][q]) / omegas[f] (H; the quantity whose error Sec. III
+ * reports). opt may be NULL (defaults), st may be NULL. Returns
+ * SVH_ERR_NOT_CONVERGED (with Zport and Lport filled) if some residual stays
+ * above rre. Requires kernels and at least one port. */
 int svh_solve(svh_handle* h, const double* omegas, int nfreq, const svh_options* opt, double* Zport,
-              svh_stats* st);
+              double* Lport, svh_stats* st);
 /* Solution vector x[N] (complex interleaved double) of port `port` at the
  * last frequency of the last svh_solve (fixed-node potentials are 0). */
 int svh_get_solution(const svh_handle* h, int port, double* x);
@@ -265,7 +268,8 @@ int svh_precond_apply(svh_handle* h, double omega, int nb, const double* in, dou
  * svh_batch_solve runs svh_solve for every structure at the same
  * frequencies with n_workers host threads (<= 0: 4), each on its own stream,
  * so one structure's host preconditioner work overlaps the others' device
- * work; Zports[i] receives structure i's nfreq*np_i*np_i complex values; the
+ * work; Zports[i] receives structure i's nfreq*np_i*np_i complex values and
+ * Lports[i] (Lports may be NULL) its inductances as in svh_solve; the
  * stats are summed (final_rre: the largest). */
 typedef struct svh_batch svh_batch;
 int svh_batch_create(svh_batch** b, int device);
@@ -278,7 +282,7 @@ int svh_batch_matvec(svh_batch* b, const double* omegas, int nb, const void* con
 int svh_batch_sync(svh_batch* b);
 void* svh_batch_stream(svh_batch* b);
 int svh_batch_solve(svh_batch* b, const double* omegas, int nfreq, const svh_options* opt, double* const* Zports,
-                    int n_workers, svh_stats* st);
+                    double* const* Lports, int n_workers, svh_stats* st);
 
 /* ---- Product for callers that cannot allocate device memory at call time.
  * (An interface of this library; the paper has no counterpart.)
@@ -291,15 +295,22 @@ int svh_batch_solve(svh_batch* b, const double* omegas, int nfreq, const svh_opt
  * array of SVH_NOALLOC_SCRATCH_BYTES (64 MiB) compiled into the library's
  * device code. Every GPU that loads the library holds that array until the
  * process exits. The call makes no cudaMalloc/cudaFree and no allocating
- * library call. Its first call on a device looks up the array's device
+ * library call; the handle's second stream and events it uses are created
+ * by svh_setup_grid. Its first call on a device looks up the array's device
  * address (cudaGetSymbolAddress); make that first call before any stream
  * capture. The scratch needs 5 * nza * Px * (Ky + Py) complex values per
  * right-hand side (nza = planes holding voxels); larger requests return
  * SVH_ERR_ARG. All calls share the one array: calls that may run
  * concurrently on the GPU (different streams or handles) race and must be
  * serialised by the caller. Nothing in the array needs clearing between
- * calls: every value a call reads it has written itself. It uses the
- * resident spectra and never runs the per-product Tucker restore. */
+ * calls: every value a call reads it has written itself. It applies the
+ * FP32 spectra on the device as they are and never runs the per-product
+ * Tucker restore: in SVH_KERNELS_TUCKER_REBUILD mode (FP32, Tucker data
+ * loaded) it returns SVH_ERR_STATE until svh_rebuild_spectra has restored
+ * them, and then applies the restored operator, as svh_matvec does. When
+ * the direct z pass is chosen but its z-space kernels have no buffers yet
+ * (svh_matvec has not run it on this handle), the call takes the FFT form
+ * of the z pass, which gives the same product. */
 #define SVH_NOALLOC_SCRATCH_BYTES (64u << 20)
 int svh_matvec_noalloc(svh_handle* h, double omega, int nb, const void* x_dev, void* y_dev, int precision);
 

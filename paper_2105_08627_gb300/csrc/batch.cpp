@@ -220,7 +220,7 @@ void* svh_batch_stream(svh_batch* bb) {
 }
 
 int svh_batch_solve(svh_batch* bb, const double* omegas, int nfreq, const svh_options* opt, double* const* Zports,
-                    int n_workers, svh_stats* st) {
+                    double* const* Lports, int n_workers, svh_stats* st) {
     Batch* b = reinterpret_cast<Batch*>(bb);
     if (!b || !omegas || nfreq <= 0 || !Zports) return b ? berr(b, SVH_ERR_ARG, "svh_batch_solve: bad arguments") : SVH_ERR_ARG;
     const int n = (int)b->items.size();
@@ -241,7 +241,8 @@ int svh_batch_solve(svh_batch* bb, const double* omegas, int nfreq, const svh_op
             cudaStream_t saved = h->stream;
             h->stream = s;
             std::memset(&sts[i], 0, sizeof(svh_stats));
-            rcs[i] = svh_solve(reinterpret_cast<svh_handle*>(h), omegas, nfreq, opt, Zports[i], &sts[i]);
+            rcs[i] = svh_solve(reinterpret_cast<svh_handle*>(h), omegas, nfreq, opt, Zports[i],
+                               Lports ? Lports[i] : nullptr, &sts[i]);
             cudaStreamSynchronize(s);
             h->stream = saved;
         }

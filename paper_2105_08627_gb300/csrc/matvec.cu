@@ -361,6 +361,19 @@ static int ensure_aux(Handle* h) {
     return SVH_OK;
 }
 
+static void ensure_smem_optin(Handle* h) {
+    if (h->smem_optin == 0) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+        h->smem_optin = (size_t)v;
+    }
+}
+
+int matvec_streams(Handle* h) {
+    ensure_smem_optin(h);
+    return ensure_aux(h);
+}
+
 int matvec_prefork(Handle* h) {
     if (int rc = ensure_aux(h)) return rc;
     SVH_CUDA_TRY(h, cudaEventRecord(h->ev_fork, h->stream));
@@ -374,13 +387,6 @@ int matvec_mark_input_ready(Handle* h) {
     return SVH_OK;
 }
 
-static void ensure_smem_optin(Handle* h) {
-    if (h->smem_optin == 0) {
-        int v = 0;
-        cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
-        h->smem_optin = (size_t)v;
-    }
-}
 
 // arguments of the size-specialised pass kernels for one product
 template <typename T>
@@ -488,8 +494,11 @@ static int run_matvec(Handle* h, double omega, const double* d_omegas, int nb, c
     ensure_smem_optin(h);
     const bool fused = ti == 0 && h->tune32[5] == 1 && fused_path_ok(pa, h->smem_optin);
     const bool rebuild = allow_rebuild && ti == 0 && h->kernel_mode == SVH_KERNELS_TUCKER_REBUILD;
-    // the direct z pass reads the z-space kernels, made from the spectra (after the restore)
-    const bool zdirect = ti == 0 && !fused && h->tune32[2] == 3 && z_direct_ok(h);
+    // the direct z pass reads the z-space kernels, made from the spectra (after the restore); a
+    // caller that may not allocate (allow_rebuild false) takes it only when those kernels' buffers
+    // exist for the current planes, and the FFT form of pass 3 otherwise
+    bool zdirect = ti == 0 && !fused && h->tune32[2] == 3 && z_direct_ok(h);
+    if (zdirect && !allow_rebuild && (!h->d_zk32.p || h->zk_D != zk_planes(h))) zdirect = false;
     cudaStream_t s = h->stream, sa = nullptr;
     if (int rc = ensure_aux(h)) return rc;
     sa = h->aux;

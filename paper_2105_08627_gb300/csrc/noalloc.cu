@@ -57,6 +57,13 @@ extern "C" int svh_matvec_noalloc(svh_handle* hh, double omega, int nb, const vo
     const char* xc = static_cast<const char*>(x);
     const char* yc = static_cast<const char*>(y);
     if (xc < yc + bytes && yc < xc + bytes) return set_err(h, SVH_ERR_ARG, "svh_matvec_noalloc: x and y overlap");
+    bool tucker = false;
+    for (int u = 0; u < 7; ++u) tucker = tucker || h->tucker_on[u];
+    if (precision == SVH_FP32 && h->kernel_mode == SVH_KERNELS_TUCKER_REBUILD && tucker &&
+        h->spec32_tk_version != h->tk_version)
+        return set_err(h, SVH_ERR_STATE,
+                       "svh_matvec_noalloc: in Tucker-restore mode the restored spectra must be on the device "
+                       "(call svh_rebuild_spectra first)");
     size_t b1, b2;
     matvec_scratch_bytes(h, nb, precision, &b1, &b2);
     const size_t b1a = (b1 + 255) & ~(size_t)255;

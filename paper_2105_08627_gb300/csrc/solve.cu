@@ -478,7 +478,7 @@ void svh_default_options(svh_options* o) {
 }
 
 int svh_solve(svh_handle* hh, const double* omegas, int nfreq, const svh_options* opt_in, double* Zport,
-              svh_stats* st) {
+              double* Lport, svh_stats* st) {
     Handle* h = reinterpret_cast<Handle*>(hh);
     if (!h) return SVH_ERR_ARG;
     cudaError_t ce = cudaSetDevice(h->device);
@@ -612,6 +612,8 @@ int svh_solve(svh_handle* hh, const double* omegas, int nfreq, const svh_options
         for (int i = 0; i < np * np; ++i) {
             Zport[((size_t)f * np * np + i) * 2] = Zi[i].real();
             Zport[((size_t)f * np * np + i) * 2 + 1] = Zi[i].imag();
+            // the port inductance L = Im(Z) / omega (Sec. II.A, the quantity of Sec. III's error)
+            if (Lport) Lport[(size_t)f * np * np + i] = Zi[i].imag() / omegas[f];
         }
     }
     // keep the solutions of the last frequency (host) for svh_get_solution and the adjoint

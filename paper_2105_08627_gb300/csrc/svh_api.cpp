@@ -264,6 +264,7 @@ static int install_kernels(Handle* h) {
     std::vector<float> s32(h->spec.begin(), h->spec.end());
     rc = dev_upload(h, h->d_spec32, s32.data(), 7 * Ht * sizeof(float));
     ++h->spec_version;
+    h->spec32_tk_version = -1;
     if (rc) return rc;
     const int P[3] = {h->Px, h->Py, h->Pz};
     const double twopi = 6.283185307179586476925286766559;
@@ -676,6 +677,7 @@ int svh_setup_grid(svh_handle* hh, int Kx, int Ky, int Kz, double dx, const uint
         const int32_t zero = 0;
         if ((rc = dev_upload(h, h->d_status, &zero, 4))) return rc;
     }
+    if ((rc = matvec_streams(h))) return rc;
     h->have_grid = true;
     return SVH_OK;
 }

@@ -62,6 +62,7 @@ struct Handle {
     std::vector<double> spec;          // [7][Hz][Hy][Hx]
     DevBuf d_spec32, d_spec64;         // float / double [7][Hz][Hy][Hx]
     int spec_version = 0;              // bumped whenever d_spec32 is rewritten
+    int spec32_tk_version = -1;        // tk_version whose Tucker restore d_spec32 holds (-1: exact spectra)
     // z-space kernels of the direct z pass: float [7][zk_D][Hy][Hx], made from d_spec32
     // with the weights d_zkw [2][zk_D][Hz] (cosines, sines); current when zk_version == spec_version
     DevBuf d_zk32, d_zkw;
@@ -139,6 +140,9 @@ void matvec_scratch_bytes(const Handle* h, int nb, int precision, size_t* b1, si
 // fork the product's second stream now (before an input copy the caller enqueues next);
 // mark_input_ready records, after that copy, the event the node rows wait for
 int matvec_prefork(Handle* h);
+// the product's second stream and its events, and the device's shared-memory limit (made once
+// per handle at grid set-up, so that no product call creates them)
+int matvec_streams(Handle* h);
 int matvec_mark_input_ready(Handle* h);
 // FFT tile variants (matvec.cu)
 int autotune(Handle* h, int nb, int32_t* variants, double* ms);

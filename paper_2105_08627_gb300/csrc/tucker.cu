@@ -533,10 +533,12 @@ int launch_tucker_rebuild(Handle* h, cudaStream_t strm, bool to_zk) {
     launch_stage(st[0], h->tk_probs_split[0], strm);
     launch_stage(st[1], h->tk_probs_split[1], strm);
     SVH_CUDA_TRY(h, cudaGetLastError());
-    if (to_zk)
+    if (to_zk) {
         h->zk_version = -2;   // the z-space kernels now come from the Tucker data, not the spectra
-    else
+    } else {
         ++h->spec_version;
+        h->spec32_tk_version = h->tk_version;
+    }
     return SVH_OK;
 }
 

@@ -97,7 +97,7 @@ SIGNATURES = {
     "svh_matvec_host": (C.c_int, [_P, C.c_double, C.c_int, _P, _P, C.c_int]),
     "svh_matvec_omegas": (C.c_int, [_P, _DP, C.c_int, _P, _P, C.c_int]),
     "svh_default_options": (None, [C.POINTER(svh_options)]),
-    "svh_solve": (C.c_int, [_P, _DP, C.c_int, C.POINTER(svh_options), _DP, C.POINTER(svh_stats)]),
+    "svh_solve": (C.c_int, [_P, _DP, C.c_int, C.POINTER(svh_options), _DP, _DP, C.POINTER(svh_stats)]),
     "svh_get_solution": (C.c_int, [_P, C.c_int, _DP]),
     "svh_precond_apply": (C.c_int, [_P, C.c_double, C.c_int, _DP, _DP]),
     "svh_set_materials": (C.c_int, [_P, _DP, _DP]),
@@ -112,8 +112,8 @@ SIGNATURES = {
     "svh_batch_matvec": (C.c_int, [_P, _DP, C.c_int, C.POINTER(_P), C.POINTER(_P), C.c_int]),
     "svh_batch_sync": (C.c_int, [_P]),
     "svh_batch_stream": (_P, [_P]),
-    "svh_batch_solve": (C.c_int, [_P, _DP, C.c_int, C.POINTER(svh_options), C.POINTER(_DP), C.c_int,
-                                  C.POINTER(svh_stats)]),
+    "svh_batch_solve": (C.c_int, [_P, _DP, C.c_int, C.POINTER(svh_options), C.POINTER(_DP), C.POINTER(_DP),
+                                  C.c_int, C.POINTER(svh_stats)]),
     "svh_profile_begin": (C.c_int, [_P, C.c_int]),
     "svh_autotune": (C.c_int, [_P, C.c_int, _I32P, _DP]),
     "svh_get_device_status": (C.c_int, [_P, _I32P, C.c_int]),
@@ -268,6 +268,7 @@ class Handle:
 
     def __init__(self, device=0, stream=None):
         self._h = _P()
+        self.device = int(device)
         rc = lib().svh_create(C.byref(self._h), int(device), _P(stream or 0))
         if rc != SVH_OK:
             raise SVHError(rc, "svh_create failed (no CUDA device?)")
@@ -433,14 +434,15 @@ class Handle:
         om = np.ascontiguousarray(2 * np.pi * freqs)
         npt = self.info()["nports"]
         Z = np.zeros((freqs.size, npt, npt, 2))
+        L = np.zeros((freqs.size, npt, npt))
         st = svh_stats()
-        rc = lib().svh_solve(self._h, _dp(om), om.size, C.byref(o), _dp(Z), C.byref(st))
+        rc = lib().svh_solve(self._h, _dp(om), om.size, C.byref(o), _dp(Z), _dp(L), C.byref(st))
         if rc != SVH_OK and not (allow and rc == SVH_ERR_NOT_CONVERGED):
             self._ck(rc, "svh_solve")
         Zc = Z[..., 0] + 1j * Z[..., 1]
         stats = {f: getattr(st, f) for f, _ in svh_stats._fields_}
         stats["status"] = rc
-        return {"Z": Zc, "L": Zc.imag / om[:, None, None], "R": Zc.real, "stats": stats}
+        return {"Z": Zc, "L": L, "R": Z[..., 0].copy(), "stats": stats}
 
     def set_materials(self, lam_vox, sigma0_vox):
         lam = np.ascontiguousarray(lam_vox, np.float64)
@@ -477,14 +479,16 @@ class Handle:
 
     FFT_PASSES = ("x_fwd", "y_fwd", "z_pass", "y_inv", "x_inv_epilogue", "path", "streams")
 
-    def autotune(self, nb):
+    def autotune(self, nb, timings=True):
         """Time every FP32 tile variant of the five FFT passes for nb items, then the
         fused y/z/y path against the separate passes, then the stream schedules, and
         keep the fastest -> (variants[7], ms per launch[7]); variants[5]: 0 separate passes,
-        1 fused; variants[6]: 0 restore + node rows overlapped, 1 node rows only, 2 one stream."""
+        1 fused; variants[6]: 0 restore + node rows overlapped, 1 node rows only, 2 one stream.
+        timings=False asks for no timings (ms is None), so that an equal grid tuned earlier in
+        the process is taken from the cache without timing anything."""
         v = np.zeros(7, np.int32)
-        ms = np.zeros(7)
-        self._ck(lib().svh_autotune(self._h, int(nb), _i32p(v), _dp(ms)), "svh_autotune")
+        ms = np.zeros(7) if timings else None
+        self._ck(lib().svh_autotune(self._h, int(nb), _i32p(v), _dp(ms) if timings else None), "svh_autotune")
         return v, ms
 
     def device_status(self, clear=True):
@@ -580,13 +584,14 @@ class Batch:
         freqs = np.atleast_1d(np.asarray(freqs, np.float64))
         om = np.ascontiguousarray(2 * np.pi * freqs)
         outs = [np.zeros((freqs.size, h.info()["nports"], h.info()["nports"], 2)) for h in self.handles]
+        Ls = [np.zeros(z.shape[:3]) for z in outs]
         ptrs = (_DP * len(outs))(*[_dp(z) for z in outs])
+        lptrs = (_DP * len(Ls))(*[_dp(l) for l in Ls])
         st = svh_stats()
-        self._ck(lib().svh_batch_solve(self._b, _dp(om), om.size, C.byref(o), ptrs, int(n_workers), C.byref(st)),
-                 "svh_batch_solve")
+        self._ck(lib().svh_batch_solve(self._b, _dp(om), om.size, C.byref(o), ptrs, lptrs, int(n_workers),
+                                       C.byref(st)), "svh_batch_solve")
         Zs = [z[..., 0] + 1j * z[..., 1] for z in outs]
-        return {"Z": Zs, "L": [z.imag / om[:, None, None] for z in Zs],
-                "stats": {f: getattr(st, f) for f, _ in svh_stats._fields_}}
+        return {"Z": Zs, "L": Ls, "stats": {f: getattr(st, f) for f, _ in svh_stats._fields_}}
 
     def close(self):
         if self._b:

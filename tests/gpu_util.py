@@ -23,12 +23,13 @@ def handle_for(structure, toeplitz=None, P=None):
     return h
 
 
-def oracle_reference(structure, P=None):
-    """(grid, S7, P) of the oracle for a structure, with its own kernels."""
+def oracle_reference(structure, P=None, processes=1):
+    """(grid, S7, P, T) of the oracle for a structure, with its own kernels (their z planes
+    integrated in `processes` spawned worker processes)."""
     g = G.build_grid(structure)
     if P is None:
         P = (op.fft_size(g.Kx), op.fft_size(g.Ky), op.fft_size(g.Kz))
-    T = gr.toeplitz_octant(g.Kx, g.Ky, g.Kz)
+    T = gr.toeplitz_octant(g.Kx, g.Ky, g.Kz, processes=processes)
     S7 = op.spectra(gr.signed_from_octant(T), P)
     return g, S7, P, T
 
