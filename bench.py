@@ -68,8 +68,8 @@ def parse():
                         "instead of running the autotuner (e.g. for profiling)")
     p.add_argument("--with-tucker-sweep", action="store_true",
                    help="add CR / CO of the Tucker-compressed spectra vs tolerance on plates and cubes")
-    p.add_argument("--with-batch", action="store_true",
-                   help="also time a graph-captured batched product over the 64 cfg-3 structures")
+    p.add_argument("--no-batch", action="store_true",
+                   help="skip the persistent batched product over the 64 cfg-3 structures")
     a = p.parse_args()
     if a.nb is None:
         a.nb = {"esfq512": 16, "meander256": 4, "pair128": 2, "strip16": 1}[a.workload]
@@ -356,10 +356,12 @@ def time_steps(h, torch, omega, x, y, steps, flush, profile=False):
 
 
 def run_batch(torch, svh, S, args):
-    """Graph-captured batched FP32 product over the 64 seeded cfg-3 structures (ports batched per item)."""
+    """The 64 seeded cfg-3 structures (uneven grids 32..128 x 32..128 x 8..16, 4-8 ports each),
+    every port at the three frequencies 1, 10, 50 GHz as its own right-hand side, all products
+    in one persistent, graph-captured launch of the batch queue."""
     items = S.batch_cfg3()
     stream = torch.cuda.current_stream().cuda_stream
-    hs, xs, ys, oms = [], [], [], []
+    hs, xs, ys, oms, kts = [], [], [], [], []
     t0 = time.perf_counter()
     for i, it in enumerate(items):
         h = svh.Handle(0, stream)
@@ -368,25 +370,20 @@ def run_batch(torch, svh, S, args):
         hs.append(h)
     setup = time.perf_counter() - t0
     b = svh.Batch(0)
-    nbs, kts = [], []
+    rhs = 0
     for i, (h, it) in enumerate(zip(hs, items)):
         b.add(h)
         info = h.info()
-        nb = max(1, info["nports"])
-        nbs.append(nb)
-        kts.append(info["Kx"] * info["Ky"] * info["Kz"])
+        nb = max(1, info["nports"]) * len(it.freqs)
+        rhs += nb
+        kts.append(nb * info["Kx"] * info["Ky"] * info["Kz"])
         xs.append(torch.from_numpy(S.random_complex(i, (nb, info["N"])).astype(np.complex64)).cuda())
         ys.append(torch.empty_like(xs[-1]))
-        oms.append(2 * np.pi * it.freqs[i % 3])
-    # the batch API takes one nb for all items: use the smallest port count
-    nb = min(nbs)
-    t1 = time.perf_counter()
-    for h in hs:
-        h.autotune(nb)                      # FFT tile variants per grid (cached for equal grids)
-    tune_s = time.perf_counter() - t1
+        oms.append(2 * np.pi * np.tile(np.asarray(it.freqs, np.float64), nb // len(it.freqs)))
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    mode_ms = b.autotune(oms, xs, ys, svh.SVH_FP32)     # persistent queue vs per-structure chains
     for _ in range(max(3, args.warmup)):
-        b.matvec(oms, xs, ys, svh.SVH_FP32, nb=nb)
+        b.matvec(oms, xs, ys, svh.SVH_FP32)
     b.sync()
     bs = torch.cuda.ExternalStream(b.stream)
     tot = 0.0
@@ -395,14 +392,19 @@ def run_batch(torch, svh, S, args):
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(bs)
-        b.matvec(oms, xs, ys, svh.SVH_FP32, nb=nb)
+        b.matvec(oms, xs, ys, svh.SVH_FP32)
         e1.record(bs)
         b.sync()
         tot += e0.elapsed_time(e1)
-    vox = nb * sum(kts)
+    vox = sum(kts)
     out = {"value": vox * args.steps / (tot / 1e3), "unit": UNIT, "ms_per_step": tot / args.steps,
-           "structures": len(items), "nb_per_structure": nb, "sum_Kt": int(sum(kts)),
-           "launch": "one CUDA graph per step (all structures)", "setup_s": setup, "autotune_s": tune_s}
+           "structures": len(items), "right_hand_sides": rhs, "sum_nb_Kt": int(vox),
+           "mode": ["persistent queue", "per-structure chains"][b.mode],
+           "autotune_ms_per_launch": {"persistent queue (one kernel)": float(mode_ms[0]),
+                                      "per-structure chains (one graph)": float(mode_ms[1])},
+           "launch": "one CUDA graph per step: mode 0 = one persistent kernel (device work queue over "
+                     "every pass of every structure), mode 1 = every structure's launch sequence on "
+                     "16 forked streams", "setup_s": setup}
     b.close()
     for h in hs:
         h.close()
@@ -532,9 +534,10 @@ def run_svh(args):
     cnt, cho = h.pass_variants()
     fused = bool(cnt[5] == 2 and cho[5] == 1)
     zdirect = not fused and int(cho[2]) == 3
+    nb_launch = nb
     zact = np.nonzero(s.occ.reshape(s.occ.shape[0], -1).any(axis=1))[0]
     zspan = int(zact[-1] - zact[0] + 1) if len(zact) else 0
-    pb = pass_bytes(info, nb, 8, fused, zk_planes=zspan if zdirect else 0)
+    pb = pass_bytes(info, nb_launch, 8, fused, zk_planes=zspan if zdirect else 0)
     dom = max((k for k in pass_ms if k != "tucker_rebuild"), key=lambda k: pass_ms[k])
     per_launch_ms = pass_ms[dom] / ncalls
     peak, peak_kind = peaks()
@@ -546,8 +549,9 @@ def run_svh(args):
                 "algorithmic_bytes_per_launch": pb[dom], "avg_launch_ms": per_launch_ms,
                 "share_of_step": pass_ms[dom] / sum(pass_ms.values()),
                 "pass_ms_per_step": {k: v / ncalls for k, v in pass_ms.items()},
-                "step_model_bytes": sum(pb.values()),
-                "step_model_frac": sum(pb.values()) / (ms / args.steps / 1e3) / 1e9 / peak}
+                "step_model_bytes": sum(pass_bytes(info, nb, 8, fused, zk_planes=zspan if zdirect else 0).values()),
+                "step_model_frac": sum(pass_bytes(info, nb, 8, fused, zk_planes=zspan if zdirect else 0).values())
+                / (ms / args.steps / 1e3) / 1e9 / peak}
     # the restore (tensor cores): TF32 MMA flops (3 per algorithmic flop) over its event time
     rf = restore_flops(info, ranks)
     t_rb = pass_ms["tucker_rebuild"] / ncalls
@@ -604,7 +608,7 @@ def run_svh(args):
     if args.with_tucker_sweep and rank == 0:
         sweep = run_tucker_sweep(torch, svh, S)
     batch = None
-    if args.with_batch and rank == 0:
+    if not args.no_batch and rank == 0:
         batch = run_batch(torch, svh, S, args)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

@@ -257,29 +257,60 @@ int svh_grad_inductance(svh_handle* h, int i, int j, double* dL_dlambda, double*
  * Schur solves run to 1e-12 (for tests). */
 int svh_precond_apply(svh_handle* h, double omega, int nb, const double* in, double* out);
 
-/* ---- Batches of independent structures (unevenly sized grids).
+/* ---- Batches of independent structures (unevenly sized grids; Sec. III's
+ * many ports and frequencies of many structures at once).
  * A batch borrows handles (each set up with its grid, ports and kernels) and
- * must be destroyed before them. svh_batch_matvec applies each structure's
- * operator to its own nb vectors x_dev[i] -> y_dev[i] (device pointers, as
- * svh_matvec) at angular frequency omegas[i]: the first call with a given
- * set of arguments runs the products once and captures all of them into one
- * CUDA graph on the batch stream; that call and later calls with the same
- * arguments launch the graph (asynchronous; svh_batch_sync waits).
+ * must be destroyed before them. svh_batch_matvec applies structure i's
+ * operator (Eq. 7 with Z by Eq. 9, as svh_matvec_omegas) to its own nbs[i]
+ * right-hand sides x_dev[i] -> y_dev[i] (device pointers, nbs[i] * N_i complex
+ * values of the precision, item r at offset r * N_i) at the angular
+ * frequencies omegas[i][0 .. nbs[i]) (host arrays, > 0). All products of the
+ * batch run in ONE persistent launch: a device work queue holds the tiles of
+ * every pass of every structure (x-forward, node rows, y-forward, z pass,
+ * y-inverse, x-inverse with the epilogue), phase by phase; each CTA takes the
+ * next tile, waits (bounded in time) until the pass that tile reads is
+ * complete for its structure, runs it and counts it done. The first call with
+ * a given argument set builds the queue (growing each handle's intermediate
+ * grids) and captures the launch in a CUDA graph on the batch stream; that
+ * call and later calls with the same arguments launch the graph
+ * (asynchronous). The spectra are each handle's resident ones (the batch
+ * runs no Tucker restore). svh_batch_sync waits for the batch stream and
+ * returns SVH_ERR_TIMEOUT (the products of that launch are incomplete, the
+ * device stays usable) when a wait of the queue ran out.
+ * svh_batch_set_wait sets the bound of each wait (limit_ms, default 1000)
+ * and, for diagnostics, a (hold_item, hold_phase) pair whose completion count
+ * is never reached (-1, -1: none; phases numbered 0 x-forward, 1 node rows,
+ * 2 y-forward, 3 z pass, 4 y-inverse, 5 x-inverse), so that the waits on it
+ * run out and the launch ends with SVH_ERR_TIMEOUT.
+ * svh_batch_set_mode selects how svh_batch_matvec runs: 0 (default) the one
+ * persistent launch above; 1 every structure's own launch sequence (the
+ * size-specialised, tile-tuned kernels of svh_matvec_omegas) on up to 16
+ * streams forked from and joined to the batch stream, captured as one CUDA
+ * graph. svh_batch_autotune times both modes on the given arguments (three
+ * graph launches each after a warm-up; ms[2], may be NULL, receives the
+ * milliseconds per launch) and keeps the faster; svh_batch_get_mode reports
+ * the current mode.
  * svh_batch_solve runs svh_solve for every structure at the same
  * frequencies with n_workers host threads (<= 0: 4), each on its own stream,
  * so one structure's host preconditioner work overlaps the others' device
  * work; Zports[i] receives structure i's nfreq*np_i*np_i complex values and
  * Lports[i] (Lports may be NULL) its inductances as in svh_solve; the
  * stats are summed (final_rre: the largest). */
+#define SVH_STATUS_QUEUE_TIMEOUT 4
 typedef struct svh_batch svh_batch;
 int svh_batch_create(svh_batch** b, int device);
 int svh_batch_destroy(svh_batch* b);
 const char* svh_batch_last_error(const svh_batch* b);
 int svh_batch_add(svh_batch* b, svh_handle* h);
 int svh_batch_size(const svh_batch* b);
-int svh_batch_matvec(svh_batch* b, const double* omegas, int nb, const void* const* x_dev, void* const* y_dev,
-                     int precision);
+int svh_batch_matvec(svh_batch* b, const int32_t* nbs, const double* const* omegas, const void* const* x_dev,
+                     void* const* y_dev, int precision);
 int svh_batch_sync(svh_batch* b);
+int svh_batch_set_wait(svh_batch* b, double limit_ms, int hold_item, int hold_phase);
+int svh_batch_set_mode(svh_batch* b, int mode);
+int svh_batch_get_mode(const svh_batch* b);
+int svh_batch_autotune(svh_batch* b, const int32_t* nbs, const double* const* omegas, const void* const* x_dev,
+                       void* const* y_dev, int precision, double* ms);
 void* svh_batch_stream(svh_batch* b);
 int svh_batch_solve(svh_batch* b, const double* omegas, int nfreq, const svh_options* opt, double* const* Zports,
                     double* const* Lports, int n_workers, svh_stats* st);

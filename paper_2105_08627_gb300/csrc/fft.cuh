@@ -17,15 +17,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "fft_plan.h"
+
 namespace svh {
-
-constexpr int MAX_STAGES = 16;
-
-struct FftPlan {
-    int N;
-    int nst;
-    int R[MAX_STAGES];
-};
 
 template <typename T> struct CT;
 template <> struct CT<float> { using type = float2; };
@@ -48,6 +42,40 @@ template <typename C, bool INV> __device__ __forceinline__ C mul_mi(C a) {
     if (INV) { c.x = -a.y; c.y = a.x; } else { c.x = a.y; c.y = -a.x; }
     return c;
 }
+
+// FP32 complex add, subtract and real scale as packed two-lane FP32 instructions
+// (add/sub/mul.rn.f32x2, sm_100 and later): one instruction per complex operation instead of
+// two, with the same round-to-nearest result in each lane. SVH_F32X2=0 keeps the scalar forms.
+#ifndef SVH_F32X2
+#define SVH_F32X2 1
+#endif
+#if SVH_F32X2
+__device__ __forceinline__ unsigned long long f2_pack(float2 a) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
+    return r;
+}
+__device__ __forceinline__ float2 f2_unpack(unsigned long long r) {
+    float2 a;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(r));
+    return a;
+}
+template <> __device__ __forceinline__ float2 cadd<float2>(float2 a, float2 b) {
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_pack(a)), "l"(f2_pack(b)));
+    return f2_unpack(d);
+}
+template <> __device__ __forceinline__ float2 csub<float2>(float2 a, float2 b) {
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_pack(a)), "l"(f2_pack(b)));
+    return f2_unpack(d);
+}
+template <> __device__ __forceinline__ float2 cscale<float2, float>(float2 a, float s) {
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_pack(a)), "l"(f2_pack(make_float2(s, s))));
+    return f2_unpack(d);
+}
+#endif
 
 // ---------------------------------------------------------------- small DFTs
 // Forward: V[k] = sum_r v[r] exp(-2 pi i r k / R); inverse uses +i.
@@ -205,7 +233,7 @@ __device__ __forceinline__ void fft_stage(C* buf, int N, int Ns, int nlines, int
 // exp(-2 pi i m / N), m = 0..N-1 (the inverse uses its conjugate).
 // Requires nlines * N <= MAXPTS * nthr. Ends with a barrier.
 template <typename C, bool INV, int MAXPTS, int LAYOUT>
-__device__ void fft_run(C* buf, const FftPlan& p, int nlines, int ld, const C* tw, int tid, int nthr) {
+__device__ __forceinline__ void fft_run(C* buf, const FftPlan& p, int nlines, int ld, const C* tw, int tid, int nthr) {
     int Ns = 1;
     for (int s = 0; s < p.nst; ++s) {
         const int R = p.R[s];

@@ -109,8 +109,12 @@ SIGNATURES = {
     "svh_batch_last_error": (C.c_char_p, [_P]),
     "svh_batch_add": (C.c_int, [_P, _P]),
     "svh_batch_size": (C.c_int, [_P]),
-    "svh_batch_matvec": (C.c_int, [_P, _DP, C.c_int, C.POINTER(_P), C.POINTER(_P), C.c_int]),
+    "svh_batch_matvec": (C.c_int, [_P, _I32P, C.POINTER(_DP), C.POINTER(_P), C.POINTER(_P), C.c_int]),
     "svh_batch_sync": (C.c_int, [_P]),
+    "svh_batch_set_wait": (C.c_int, [_P, C.c_double, C.c_int, C.c_int]),
+    "svh_batch_set_mode": (C.c_int, [_P, C.c_int]),
+    "svh_batch_get_mode": (C.c_int, [_P]),
+    "svh_batch_autotune": (C.c_int, [_P, _I32P, C.POINTER(_DP), C.POINTER(_P), C.POINTER(_P), C.c_int, _DP]),
     "svh_batch_stream": (_P, [_P]),
     "svh_batch_solve": (C.c_int, [_P, _DP, C.c_int, C.POINTER(svh_options), C.POINTER(_DP), C.POINTER(_DP),
                                   C.c_int, C.POINTER(svh_stats)]),
@@ -563,11 +567,43 @@ class Batch:
         self._ck(lib().svh_batch_add(self._b, handle._h), "svh_batch_add")
         self.handles.append(handle)
 
-    def matvec(self, omegas, xs, ys, precision=SVH_FP32, nb=1):
-        om = np.ascontiguousarray(omegas, np.float64)
+    def _args(self, omegas, xs, ys):
+        nbs = np.array([1 if x.dim() == 1 else x.shape[0] for x in xs], np.int32)
+        oms = [np.ascontiguousarray(np.broadcast_to(np.asarray(o, np.float64), (int(n),)))
+               for o, n in zip(omegas, nbs)]
+        self._keep = (nbs, oms)
+        op = (_DP * len(oms))(*[_dp(o) for o in oms])
         xp = (_P * len(xs))(*[x.data_ptr() for x in xs])
         yp = (_P * len(ys))(*[y.data_ptr() for y in ys])
-        self._ck(lib().svh_batch_matvec(self._b, _dp(om), nb, xp, yp, precision), "svh_batch_matvec")
+        return nbs, op, xp, yp
+
+    def matvec(self, omegas, xs, ys, precision=SVH_FP32):
+        """Every structure's product in one graph launch (mode 0: the persistent queue; mode 1:
+        the structures' own launch sequences): xs[i], ys[i] are contiguous CUDA tensors of shape
+        (nb_i, N_i) (or (N_i,)); omegas[i] holds nb_i angular frequencies (or one for all)."""
+        nbs, op, xp, yp = self._args(omegas, xs, ys)
+        self._ck(lib().svh_batch_matvec(self._b, _i32p(nbs), op, xp, yp, precision), "svh_batch_matvec")
+
+    def set_mode(self, mode):
+        self._ck(lib().svh_batch_set_mode(self._b, int(mode)), "svh_batch_set_mode")
+
+    @property
+    def mode(self):
+        return lib().svh_batch_get_mode(self._b)
+
+    def autotune(self, omegas, xs, ys, precision=SVH_FP32):
+        """Times both modes on these arguments, keeps the faster -> ms per launch [mode 0, mode 1]."""
+        nbs, op, xp, yp = self._args(omegas, xs, ys)
+        ms = np.zeros(2)
+        self._ck(lib().svh_batch_autotune(self._b, _i32p(nbs), op, xp, yp, precision, _dp(ms)),
+                 "svh_batch_autotune")
+        return ms
+
+    def set_wait(self, limit_ms, hold_item=-1, hold_phase=-1):
+        """Bound of each wait of the batch queue; (hold_item, hold_phase) names a pass whose
+        completion is never counted (diagnostics: the launch then ends with SVH_ERR_TIMEOUT)."""
+        self._ck(lib().svh_batch_set_wait(self._b, float(limit_ms), int(hold_item), int(hold_phase)),
+                 "svh_batch_set_wait")
 
     def sync(self):
         self._ck(lib().svh_batch_sync(self._b), "svh_batch_sync")

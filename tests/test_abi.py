@@ -105,3 +105,44 @@ def test_toeplitz_store_crop_and_errors(svh, tmp_path):
     bad.write_bytes(b"not a store" * 8)
     with pytest.raises(svh.SVHError):
         svh.toeplitz_store_read(str(bad), (4, 4, 4))
+
+
+# ---------------------------------------------------------------- failures made on the host
+def test_null_handle_and_null_arrays_are_rejected(svh):
+    """Every handle call checks its handle before touching a device; host utilities check their
+    arrays (no GPU is needed for either)."""
+    import ctypes as C
+    L = svh.lib()
+    null = svh._P()
+    z = (C.c_double * 4)()
+    opt = svh.svh_options()
+    L.svh_default_options(C.byref(opt))
+    assert L.svh_solve(null, z, 1, C.byref(opt), z, z, None) == svh.SVH_ERR_ARG
+    assert L.svh_matvec(null, 1e9, 1, None, None, svh.SVH_FP32) == svh.SVH_ERR_ARG
+    assert L.svh_matvec_noalloc(null, 1e9, 1, None, None, svh.SVH_FP32) == svh.SVH_ERR_ARG
+    assert L.svh_grad_inductance(null, 0, 0, z, z) == svh.SVH_ERR_ARG
+    assert L.svh_set_materials(null, z, z) == svh.SVH_ERR_ARG
+    assert L.svh_get_solution(null, 0, z) == svh.SVH_ERR_ARG
+    K = C.c_int64()
+    assert L.svh_host_face_nodes(2, 2, 2, None, C.byref(K), C.byref(K), None) == svh.SVH_ERR_ARG
+    assert L.svh_host_spectra(2, 2, 2, 4, 4, 4, None, z) == svh.SVH_ERR_ARG
+    assert L.svh_host_spectra(2, 2, 2, 2, 4, 4, z, z) == svh.SVH_ERR_ARG        # P < 2K - 1
+    d = (C.c_int32 * 3)()
+    assert L.svh_host_tucker_svd(z, 2, 2, 1, -1.0, d, z, z, z, z) == svh.SVH_ERR_ARG
+    assert L.svh_host_amg_solve(0, None, None, None, None, None, 1e-8, 10, None, None) == svh.SVH_ERR_ARG
+
+
+def test_host_amg_stops_at_maxit_with_not_converged(svh):
+    """A CG that runs out of iterations reports SVH_ERR_NOT_CONVERGED (the Schur solves of the
+    preconditioner, Eq. 14)."""
+    import scipy.sparse as sp
+    n = 4000
+    rng = np.random.default_rng(3)
+    main = 2.0 + 1e-6 * rng.random(n)
+    S_ = sp.diags([-np.ones(n - 1), main, -np.ones(n - 1)], [-1, 0, 1], format="csr")   # 1-D Laplacian
+    b = rng.standard_normal(n)
+    with pytest.raises(svh.SVHError) as e:
+        svh.host_amg_solve(S_, b, tol=1e-14, maxit=1)
+    assert e.value.code == svh.SVH_ERR_NOT_CONVERGED
+    x, it, lv = svh.host_amg_solve(S_, b, tol=1e-8, maxit=500)
+    assert np.linalg.norm(S_ @ x - b) <= 2e-8 * np.linalg.norm(b)

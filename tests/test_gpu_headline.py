@@ -65,7 +65,11 @@ def test_esfq512_bench_path_dense_input():
 
     check(h.matvec(om, xd), f"autotuned tiles {tiles.tolist()}")
     assert h.device_status() == 0
-    counts, _ = h.pass_variants()
+    counts, chosen = h.pass_variants()
+    for sched in range(counts[6]):                   # stream schedules (two item groups: 3)
+        h.set_pass_variant(6, sched)
+        check(h.matvec(om, xd), f"schedule {sched}")
+    h.set_pass_variant(6, int(chosen[6]))
     for zv in range(counts[2]):                      # every z-pass form at Pz = 48
         h.set_pass_variant(2, zv)
         check(h.matvec(om, xd), f"z variant {zv}")
@@ -99,7 +103,7 @@ def test_meander256_bench_path_dense_input():
         h.set_pass_variant(2, zv)
         check(f"z variant {zv}")
     h.set_pass_variant(2, int(chosen[2]))
-    for sched in range(3):                           # stream schedules with the restore
+    for sched in range(counts[6]):                   # stream schedules with the restore
         h.set_pass_variant(6, sched)
         check(f"schedule {sched}")
     h.close()
