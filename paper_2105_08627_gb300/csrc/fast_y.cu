@@ -5,8 +5,10 @@
 //   1: the same split with 512 threads (twice the kx columns per block),
 //   2: the same split with 128 threads,
 //   3: the transposed split N2 x N1 with 256 threads (sizes where both
-//      factors suit the pruned first and second stages).
+//      factors suit the pruned first and second stages; elsewhere 3 runs 0),
+//   4: the cp.async-staged persistent kernel k_ycol_async, 8 kx columns per tile (sizes >= 256).
 // FP64 has variant 0 only (128 threads).
+#include <algorithm>
 #include <type_traits>
 
 #include "fastpass.cuh"
@@ -24,6 +26,22 @@ static void run_y(const PassArgs& a, cudaStream_t s) {
     k_ycol_fast<T, N1, N2, INV, NT><<<grid, NT, sm, s>>>(a);
 }
 
+// variant 4: the cp.async-staged persistent kernel (FP32), as many blocks as fit an SM
+template <int N1, int N2, bool INV, int NT>
+static void run_y_async(const PassArgs& a, cudaStream_t s) {
+    constexpr int TB = NT / N2;
+    constexpr int N = N1 * N2;
+    const size_t sm = (size_t)(N + (INV ? N : N / 2) * TB + N * TB) * sizeof(float2);
+    cudaFuncSetAttribute(k_ycol_async<N1, N2, INV, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ycol_async<N1, N2, INV, NT>, NT, sm);
+    const int ntiles = ((a.Px + TB - 1) / TB) * a.nza * a.nb * 5;
+    const int grid = std::max(1, std::min(ntiles, std::max(1, sms) * std::max(1, per_sm)));
+    k_ycol_async<N1, N2, INV, NT><<<grid, NT, sm, s>>>(a, ntiles);
+}
+
 // N1 x N2 default split; SWAP: the transposed split is a variant too
 template <typename T, bool INV, int N1, int N2, bool SWAP>
 static bool run_y_size(const PassArgs& a, cudaStream_t s) {
@@ -33,6 +51,11 @@ static bool run_y_size(const PassArgs& a, cudaStream_t s) {
             case 2: run_y<T, N1, N2, INV, 128>(a, s); return true;
             case 3:
                 if constexpr (SWAP) { run_y<T, N2, N1, INV, 256>(a, s); return true; }
+                break;
+            case 4:
+                // (whole 16-byte column pairs: Px a multiple of the 8-column tile)
+                if constexpr (N1 * N2 >= 256 && N2 <= 64)
+                    if (a.Px % 8 == 0) { run_y_async<N1, N2, INV, 8 * N2>(a, s); return true; }
                 break;
             default: break;
         }
@@ -64,9 +87,10 @@ static bool dispatch_y(const PassArgs& a, cudaStream_t s) {
 
 int y_fast_variants(int Py, bool fp32) {
     if (!fp32) return 1;
-    switch (Py) {
-        case 32: case 128: case 512: return 4;
-        case 16: case 48: case 64: case 96: case 192: case 256: case 384: case 768: case 1024: return 3;
+    switch (Py) {   // 4: the cp.async-staged kernel (sizes >= 256; where 3 has no transposed split it runs 0)
+        case 256: case 384: case 512: case 768: case 1024: return 5;
+        case 32: case 128: return 4;
+        case 16: case 48: case 64: case 96: case 192: return 3;
         default: return 0;
     }
 }

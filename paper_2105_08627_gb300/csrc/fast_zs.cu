@@ -21,6 +21,8 @@
 
 namespace svh {
 
+bool z_split_ok(int Pz, int nza, int zcontig) { return (Pz == 32 || Pz == 48) && zcontig && 2 * nza <= Pz; }
+
 template <int PZ>
 __global__ void __launch_bounds__(320, 2) k_zpass_split(const __grid_constant__ PassArgs a) {
     using C = float2;
@@ -97,14 +99,131 @@ __global__ void __launch_bounds__(320, 2) k_zpass_split(const __grid_constant__ 
     }
 }
 
+// Variant 5: the same split-pencil transform on tiles of TC kx columns (TC = 16: blocks of
+// 160 threads, half the shared memory, twice the blocks per SM), with the tile's spectra packed
+// per frequency point as two float4 (G00, Sx, Sy, Sz | Qx, Qy, Qz, 0): two 16-byte shared loads
+// per point instead of seven.
+template <int PZ, int TC>
+__global__ void __launch_bounds__(10 * TC, 4) k_zpass_split4(const __grid_constant__ PassArgs a) {
+    using C = float2;
+    constexpr int NT = 10 * TC, H = PZ / 2, Q = H / 2, TS = 96 / PZ, NH = PZ / 2 + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C(*buf)[2][H][TC] = reinterpret_cast<C(*)[2][H][TC]>(smem_raw);   // [5][parity][k][column]
+    float4(*sp)[PZ][TC] = reinterpret_cast<float4(*)[PZ][TC]>(smem_raw + sizeof(C) * 5 * 2 * H * TC);  // [2][kz][col]
+    const int q = threadIdx.x / TC, lane = threadIdx.x % TC;
+    const int al = q >> 1, par = q & 1;
+    const int kx0 = blockIdx.x * TC, ky = blockIdx.y, kx = kx0 + lane;
+    const bool ok = kx < a.Px;
+    {
+        // spectra of the tile with the odd-kernel signs folded in (Sx by column, Sy by row, Sz by
+        // the upper half of kz); each octant value is loaded once
+        const float* spec = static_cast<const float*>(a.spec);
+        const int64_t plane = (int64_t)a.Hx * a.Hy, Sk = plane * a.Hz;
+        const int ay = min(ky, a.Py - ky);
+        const float sgy = (2 * ky <= a.Py) ? 1.f : -1.f;
+        float* spf = reinterpret_cast<float*>(sp);
+        for (int task = threadIdx.x; task < 7 * TC; task += NT) {
+            const int u = task / TC, ln = task % TC;
+            const int kxx = min(kx0 + ln, a.Px - 1);
+            const int ax = min(kxx, a.Px - kxx);
+            const float sgx = (2 * kxx <= a.Px) ? 1.f : -1.f;
+            const float sg = u == 1 ? sgx : (u == 2 ? sgy : 1.f);
+            const int64_t off = (int64_t)ay * a.Hx + ax;
+            const int half = u / 4, comp = u % 4;
+            float val[NH];
+#pragma unroll
+            for (int az = 0; az < NH; ++az) val[az] = __ldg(spec + u * Sk + az * plane + off);
+#pragma unroll
+            for (int az = 0; az < NH; ++az) {
+                spf[((half * PZ + az) * TC + ln) * 4 + comp] = sg * val[az];
+                if (az > 0 && PZ - az != az) spf[((half * PZ + PZ - az) * TC + ln) * 4 + comp] = (u == 3 ? -sg : sg) * val[az];
+            }
+        }
+        for (int i = threadIdx.x; i < PZ * TC; i += NT) spf[((PZ + i / TC) * TC + i % TC) * 4 + 3] = 0.f;
+    }
+    C* B2 = static_cast<C*>(a.B2);
+    const int64_t plane = (int64_t)a.Py * a.Px;
+    const int nza = a.nza;
+    C pre[Q];
+    auto fetch = [&](int b) {
+        const int64_t base = ((int64_t)(b * 5 + al) * nza * a.Py + ky) * a.Px + kx;
+#pragma unroll
+        for (int m = 0; m < Q; ++m) {
+            const int zi = 2 * m + par;
+            C z;
+            z.x = 0;
+            z.y = 0;
+            if (ok && zi < nza) z = B2[base + zi * plane];
+            pre[m] = z;
+        }
+    };
+    fetch(0);
+    for (int b = 0; b < a.nb; ++b) {
+        {
+            C v[H];
+            reg_fft_lowin<H, false>(pre, v);
+            if (b + 1 < a.nb) fetch(b + 1);
+            // a thread writes only its own (basis, parity, column) line here, which after the
+            // previous item's second barrier only it reads: no barrier is needed before this
+#pragma unroll
+            for (int k = 0; k < H; ++k) buf[al][par][k][lane] = (par && k) ? cmul(v[k], w96<C>(k * TS)) : v[k];
+        }
+        __syncthreads();
+        for (int task = threadIdx.x; task < H * TC; task += NT) {
+            const int k = task / TC, ln = task % TC;
+            C lo[5], hi[5];
+#pragma unroll
+            for (int p = 0; p < 5; ++p) {
+                const C e = buf[p][0][k][ln], o = buf[p][1][k][ln];
+                lo[p] = cadd(e, o);
+                hi[p] = csub(e, o);
+            }
+            const float4 l0 = sp[0][k][ln], l1 = sp[1][k][ln], h0 = sp[0][k + H][ln], h1 = sp[1][k + H][ln];
+            block_multiply5<float>(lo, l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z);
+            block_multiply5<float>(hi, h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z);
+#pragma unroll
+            for (int p = 0; p < 5; ++p) {
+                buf[p][0][k][ln] = cadd(lo[p], hi[p]);
+                const C d = csub(lo[p], hi[p]);
+                buf[p][1][k][ln] = k ? cmulc(d, w96<C>(k * TS)) : d;
+            }
+        }
+        __syncthreads();
+        C v[H], w[Q];
+#pragma unroll
+        for (int k = 0; k < H; ++k) v[k] = buf[al][par][k][lane];
+        reg_fft_lowout<H, true>(v, w);
+        if (ok) {
+            const int64_t base = ((int64_t)(b * 5 + al) * nza * a.Py + ky) * a.Px + kx;
+#pragma unroll
+            for (int m = 0; m < Q; ++m) {
+                const int zi = 2 * m + par;
+                if (zi < nza) B2[base + zi * plane] = w[m];
+            }
+        }
+    }
+}
+
+template <int PZ, int TC>
+static void run_zsplit4(const PassArgs& a, cudaStream_t s) {
+    const size_t sm = (size_t)5 * PZ * TC * sizeof(float2) + (size_t)2 * PZ * TC * sizeof(float4);
+    cudaFuncSetAttribute(k_zpass_split4<PZ, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_zpass_split4<PZ, TC><<<dim3((unsigned)((a.Px + TC - 1) / TC), (unsigned)a.Py), 10 * TC, sm, s>>>(a);
+}
+
+bool launch_z_split16(const PassArgs& a, cudaStream_t s) {
+    if (!z_split_ok(a.Pz, a.nza, a.zcontig)) return false;
+    if (a.Pz == 32) run_zsplit4<32, 16>(a, s);
+    else run_zsplit4<48, 16>(a, s);
+    return true;
+}
+
 template <int PZ>
 static void run_zsplit(const PassArgs& a, cudaStream_t s) {
     const size_t sm = (size_t)5 * PZ * 32 * sizeof(float2) + (size_t)7 * PZ * 32 * sizeof(float);
     cudaFuncSetAttribute(k_zpass_split<PZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_zpass_split<PZ><<<dim3((unsigned)((a.Px + 31) / 32), (unsigned)a.Py), 320, sm, s>>>(a);
 }
-
-bool z_split_ok(int Pz, int nza, int zcontig) { return (Pz == 32 || Pz == 48) && zcontig && 2 * nza <= Pz; }
 
 bool launch_z_split(const PassArgs& a, cudaStream_t s) {
     if (!z_split_ok(a.Pz, a.nza, a.zcontig)) return false;

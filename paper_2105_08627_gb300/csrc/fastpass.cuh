@@ -433,6 +433,112 @@ __global__ void __launch_bounds__(NT) k_ycol_fast(const __grid_constant__ PassAr
     }
 }
 
+// ---------------------------------------------------------------- y passes, staged by cp.async
+// The same four-step transform as k_ycol_fast (FP32), run by a persistent grid whose blocks walk
+// the (item*basis, plane, kx tile) tiles with a stride of the grid size (kx tile fastest, so the
+// grid sweeps one plane together). A tile's input rows travel by cp.async (16 bytes = two
+// columns per copy, zero-filled for rows without voxels) into a shared buffer; as soon as the
+// first stage has read the current tile from it, the copies of the block's NEXT tile are issued,
+// so they land while this tile is twiddled, exchanged, transformed and stored.
+template <int N1, int N2, bool INV, int NT>
+__global__ void __launch_bounds__(NT) k_ycol_async(const __grid_constant__ PassArgs a, int ntiles) {
+    using C = float2;
+    constexpr int N = N1 * N2;
+    constexpr int TB = NT / N2;                 // kx columns per tile (even)
+    constexpr int NROW = INV ? N : N / 2;        // input rows of a tile (forward: y < Ky <= N / 2)
+    constexpr int SEG = TB / 2;                  // 16-byte segments per row
+    constexpr int CPT = (NROW * SEG + NT - 1) / NT;
+    constexpr int TPT = (TB * N1 + NT - 1) / NT;
+    static_assert(TB % 2 == 0, "two columns per 16-byte copy");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* tw = reinterpret_cast<C*>(smem_raw);
+    C* in = tw + N;                              // [NROW][TB]
+    C* buf = in + NROW * TB;                     // [n2][k1][TB]
+    const C* twg = static_cast<const C*>(a.twy);
+    for (int i = threadIdx.x; i < N; i += NT) tw[i] = twg[i];
+    const int Px = a.Px, Ky = a.Ky, nza = a.nza;
+    const int nkx = (Px + TB - 1) / TB;
+    // the launcher takes this kernel only when Px is a multiple of TB: a tile's columns are all in range
+    auto issue = [&](int t) {
+        const int kxt = t % nkx, r = t / nkx;
+        const int zi = r % nza;
+        const int64_t ba = r / nza;
+        const C* src = static_cast<const C*>(INV ? a.B2 : a.B1) +
+                       ((ba * nza + zi) * (int64_t)(INV ? N : Ky)) * Px + (int64_t)kxt * TB;
+        const uint8_t* rm = a.rowmask + (int64_t)zi * Ky;
+#pragma unroll
+        for (int i = 0; i < CPT; ++i) {
+            const int e = threadIdx.x + i * NT;
+            if (e < NROW * SEG) {
+                const int row = e / SEG, sg = e % SEG;
+                const bool valid = INV || (row < Ky && __ldg(rm + row));
+                cp_async16_zfill(in + row * TB + 2 * sg, src + (int64_t)(valid ? row : 0) * Px + 2 * sg, valid);
+            }
+        }
+        cp_async_commit();
+    };
+    const int c = threadIdx.x % TB, n2 = threadIdx.x / TB;
+    int t = blockIdx.x;
+    if (t < ntiles) issue(t);
+    cp_async_wait<0>();
+    __syncthreads();
+    for (; t < ntiles; t += gridDim.x) {
+        C v[N1];
+        if constexpr (!INV) {
+            C hv[N1 / 2];
+#pragma unroll
+            for (int n1 = 0; n1 < N1 / 2; ++n1) hv[n1] = in[(n1 * N2 + n2) * TB + c];
+            reg_fft_lowin<N1, false>(hv, v);
+        } else {
+#pragma unroll
+            for (int n1 = 0; n1 < N1; ++n1) v[n1] = in[(n1 * N2 + n2) * TB + c];
+            reg_fft<N1, true>(v);
+        }
+        const int kxt = t % nkx, r = t / nkx;
+        const int zi = r % nza;
+        const int64_t ba = r / nza;
+        const int kx0 = kxt * TB;
+        __syncthreads();                                 // every read of `in` is done
+        if (t + (int)gridDim.x < ntiles) issue(t + gridDim.x);   // the next tile's rows, in flight
+#pragma unroll
+        for (int k1 = 1; k1 < N1; ++k1) {
+            const int m = (n2 * k1) % N;
+            if (m) v[k1] = INV ? cmulc(v[k1], tw[m]) : cmul(v[k1], tw[m]);
+        }
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) buf[(n2 * N1 + k1) * TB + c] = v[k1];
+        __syncthreads();
+#pragma unroll
+        for (int it = 0; it < TPT; ++it) {
+            const int task = threadIdx.x + it * NT;
+            if (task >= TB * N1) break;
+            const int cc = task % TB, k1 = task / TB;
+            C u[N2];
+#pragma unroll
+            for (int q = 0; q < N2; ++q) u[q] = buf[(q * N1 + k1) * TB + cc];
+            if constexpr (!INV) {
+                reg_fft<N2, false>(u);
+                C* dst = static_cast<C*>(a.B2) + ((ba * nza + zi) * (int64_t)N) * Px + kx0 + cc;
+#pragma unroll
+                for (int k2 = 0; k2 < N2; ++k2) dst[(int64_t)(k1 + N1 * k2) * Px] = u[k2];
+            } else {
+                // only y = k1 + N1 k2 < Ky <= N / 2 is kept: k2 < N2 / 2 (output-pruned)
+                C w[N2 / 2];
+                reg_fft_lowout<N2, true>(u, w);
+                C* dst = static_cast<C*>(a.B1) + ((ba * nza + zi) * (int64_t)Ky) * Px + kx0 + cc;
+                const uint8_t* rm = a.rowmask + (int64_t)zi * Ky;
+#pragma unroll
+                for (int k2 = 0; k2 < N2 / 2; ++k2) {
+                    const int k = k1 + N1 * k2;
+                    if (k < Ky && __ldg(rm + k)) dst[(int64_t)k * Px] = w[k2];
+                }
+            }
+        }
+        cp_async_wait<0>();                              // the next tile's rows have landed
+        __syncthreads();                                 // and every read of buf is done
+    }
+}
+
 // ---------------------------------------------------------------- z pass (whole pencils per thread)
 // Block: 5 warps (warp = basis alpha), lane = kx offset in a 32-wide tile, one ky.
 template <typename T>
@@ -751,6 +857,7 @@ bool launch_z_direct(const PassArgs& a, cudaStream_t s);
 // planes consecutive and in the lower half
 bool z_split_ok(int Pz, int nza, int zcontig);
 bool launch_z_split(const PassArgs& a, cudaStream_t s);
+bool launch_z_split16(const PassArgs& a, cudaStream_t s);
 void launch_spec_to_zk(const float* S, float* R, const float* W, int Hx, int Hy, int Hz, int D, cudaStream_t s);
 bool z_fast_size(int Pz);
 // number of tile variants of a pass at this size (0: no specialised kernel)

@@ -300,36 +300,46 @@ __global__ void __launch_bounds__(NTHR) k_xinv(
 }
 
 // ------------------------------------------------------------------ current-continuity rows
+// one thread per node m: its two incidences (voxel, face) are read once, then every item's
+// continuity row is formed from them (the items' loads are independent and overlap)
 template <typename T>
 __global__ void k_nodes(const typename CT<T>::type* __restrict__ x, typename CT<T>::type* __restrict__ y,
                         int64_t Nvec, int64_t K, int64_t M, int nb, const int32_t* __restrict__ ninc,
                         const uint8_t* __restrict__ freem, int masked) {
     using C = typename CT<T>::type;
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= M * nb) return;
-    int64_t b = i / M, m = i - b * M;
-    const C* xb = x + b * Nvec;
-    C acc = czero<C>();
-    if (masked && !freem[m]) {
-        acc = xb[5 * K + m];
-    } else {
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    const bool fixed = masked && !freem[m];
+    int64_t off[2][5];
+    float fl[2][5];
 #pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            int code = ninc[m * 2 + e];
-            if (code < 0) continue;
-            int v = code / 6, f = code - 6 * v;
+    for (int e = 0; e < 2; ++e) {
+        const int code = __ldg(ninc + m * 2 + e);
+        const int v = code < 0 ? 0 : code / 6, f = code < 0 ? 0 : code - 6 * (code / 6);
 #pragma unroll
-            for (int a = 0; a < 5; ++a) {
-                float fl = c_flux[a][f];
-                if (fl != 0.f) {
-                    C I = xb[a * K + v];
-                    acc.x += (T)fl * I.x;
-                    acc.y += (T)fl * I.y;
-                }
-            }
+        for (int a = 0; a < 5; ++a) {
+            fl[e][a] = code < 0 || fixed ? 0.f : c_flux[a][f];
+            off[e][a] = a * K + v;
         }
     }
-    y[b * Nvec + 5 * K + m] = acc;
+    for (int b = 0; b < nb; ++b) {
+        const C* xb = x + (int64_t)b * Nvec;
+        C acc = czero<C>();
+        if (fixed) {
+            acc = xb[5 * K + m];
+        } else {
+#pragma unroll
+            for (int e = 0; e < 2; ++e)
+#pragma unroll
+                for (int a = 0; a < 5; ++a)
+                    if (fl[e][a] != 0.f) {
+                        const C I = xb[off[e][a]];
+                        acc.x += (T)fl[e][a] * I.x;
+                        acc.y += (T)fl[e][a] * I.y;
+                    }
+        }
+        y[(int64_t)b * Nvec + 5 * K + m] = acc;
+    }
 }
 
 // ------------------------------------------------------------------ host launcher
@@ -358,6 +368,12 @@ static int ensure_aux(Handle* h) {
     SVH_CUDA_TRY(h, cudaEventCreateWithFlags(&h->ev_spec, cudaEventDisableTiming));
     SVH_CUDA_TRY(h, cudaEventCreateWithFlags(&h->ev_done, cudaEventDisableTiming));
     SVH_CUDA_TRY(h, cudaEventCreateWithFlags(&h->ev_x, cudaEventDisableTiming));
+    SVH_CUDA_TRY(h, cudaStreamCreateWithFlags(&h->cpy_in, cudaStreamNonBlocking));
+    SVH_CUDA_TRY(h, cudaStreamCreateWithFlags(&h->cpy_out, cudaStreamNonBlocking));
+    for (int j = 0; j < kHostChunks; ++j) {
+        SVH_CUDA_TRY(h, cudaEventCreateWithFlags(&h->ev_in[j], cudaEventDisableTiming));
+        SVH_CUDA_TRY(h, cudaEventCreateWithFlags(&h->ev_out[j], cudaEventDisableTiming));
+    }
     return SVH_OK;
 }
 
@@ -465,7 +481,12 @@ static int ensure_zk(Handle* h, cudaStream_t s, bool force, bool alloc_only = fa
 // The launch sequence on caller-provided intermediate grids B1, B2.
 template <typename T>
 static int run_matvec(Handle* h, double omega, const double* d_omegas, int nb, const void* xv, void* yv, int masked,
-                      void* B1v, void* B2v, bool allow_rebuild) {
+                      void* B1v, void* B2v, int kmode) {
+    // kmode 0: the kernels as the handle's mode asks (restore in rebuild mode, z-space kernels
+    // refreshed); 1: the caller may not allocate (no restore; the direct z pass only when its
+    // buffers exist); 2: reuse the kernels a product earlier in the same call prepared (no
+    // restore, no refresh: the later chunks of the host-buffer entry point)
+    const bool allow_rebuild = kmode == 0;
     using C = typename CT<T>::type;
     constexpr int MAXPTS = Cfg<T>::MAXPTS;
     const C* x = static_cast<const C*>(xv);
@@ -498,7 +519,7 @@ static int run_matvec(Handle* h, double omega, const double* d_omegas, int nb, c
     // caller that may not allocate (allow_rebuild false) takes it only when those kernels' buffers
     // exist for the current planes, and the FFT form of pass 3 otherwise
     bool zdirect = ti == 0 && !fused && h->tune32[2] == 3 && z_direct_ok(h);
-    if (zdirect && !allow_rebuild && (!h->d_zk32.p || h->zk_D != zk_planes(h))) zdirect = false;
+    if (zdirect && kmode == 1 && (!h->d_zk32.p || h->zk_D != zk_planes(h))) zdirect = false;
     cudaStream_t s = h->stream, sa = nullptr;
     if (int rc = ensure_aux(h)) return rc;
     sa = h->aux;
@@ -525,7 +546,7 @@ static int run_matvec(Handle* h, double omega, const double* d_omegas, int nb, c
         if (!rc_aux) rc_aux = launch_tucker_rebuild(h, s_rb, true);
     } else if (rebuild) {
         rc_aux = launch_tucker_rebuild(h, s_rb, false);
-    } else if (zdirect) {
+    } else if (zdirect && kmode != 2) {
         rc_aux = ensure_zk(h, s_rb, false);
     }
     pa.zk = static_cast<const float*>(h->d_zk32.p);
@@ -539,7 +560,7 @@ static int run_matvec(Handle* h, double omega, const double* d_omegas, int nb, c
     }
     if (s_nd == sa) {
         prof_at(h, 6, 0, sa);
-        int64_t n = M * nb;
+        int64_t n = M;
         k_nodes<T><<<(unsigned)((n + 255) / 256), 256, 0, sa>>>(
             x, y, Nvec, K, M, nb, static_cast<const int32_t*>(h->d_ninc.p),
             static_cast<const uint8_t*>(h->d_free.p), masked);
@@ -633,7 +654,7 @@ static int run_matvec(Handle* h, double omega, const double* d_omegas, int nb, c
     }
     if (s_nd == s) {
         prof_at(h, 6, 0, s);
-        int64_t n = M * nb;
+        int64_t n = M;
         k_nodes<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
             x, y, Nvec, K, M, nb, static_cast<const int32_t*>(h->d_ninc.p),
             static_cast<const uint8_t*>(h->d_free.p), masked);
@@ -649,12 +670,18 @@ static int run_matvec(Handle* h, double omega, const double* d_omegas, int nb, c
 
 // The library-allocated path: grows the handle's intermediate grids when needed.
 template <typename T>
-static int launch_matvec(Handle* h, double omega, int nb, const void* xv, void* yv, int masked, const double* d_omegas) {
+static int launch_matvec(Handle* h, double omega, int nb, const void* xv, void* yv, int masked, const double* d_omegas,
+                         int kmode = 0) {
     size_t b1, b2;
     matvec_scratch_bytes(h, nb, std::is_same<T, float>::value ? SVH_FP32 : SVH_FP64, &b1, &b2);
     if (h->d_B1.bytes < b1) { int rc = dev_alloc(h, h->d_B1, b1); if (rc) return rc; }
     if (h->d_B2.bytes < b2) { int rc = dev_alloc(h, h->d_B2, b2); if (rc) return rc; }
-    return run_matvec<T>(h, omega, d_omegas, nb, xv, yv, masked, h->d_B1.p, h->d_B2.p, true);
+    return run_matvec<T>(h, omega, d_omegas, nb, xv, yv, masked, h->d_B1.p, h->d_B2.p, kmode);
+}
+
+int launch_matvec_reuse(Handle* h, double omega, int nb, const void* x, void* y, int precision) {
+    return precision == SVH_FP32 ? launch_matvec<float>(h, omega, nb, x, y, 0, nullptr, 2)
+                                 : launch_matvec<double>(h, omega, nb, x, y, 0, nullptr, 2);
 }
 
 int launch_matvec32(Handle* h, double omega, int nb, const void* x, void* y, int masked, const double* d_omegas) {
@@ -664,8 +691,8 @@ int launch_matvec64(Handle* h, double omega, int nb, const void* x, void* y, int
     return launch_matvec<double>(h, omega, nb, x, y, masked, d_omegas);
 }
 int launch_matvec_on(Handle* h, double omega, int nb, const void* x, void* y, int precision, void* B1, void* B2) {
-    return precision == SVH_FP32 ? run_matvec<float>(h, omega, nullptr, nb, x, y, 0, B1, B2, false)
-                                 : run_matvec<double>(h, omega, nullptr, nb, x, y, 0, B1, B2, false);
+    return precision == SVH_FP32 ? run_matvec<float>(h, omega, nullptr, nb, x, y, 0, B1, B2, 1)
+                                 : run_matvec<double>(h, omega, nullptr, nb, x, y, 0, B1, B2, 1);
 }
 
 // ---- FFT tile autotuning
@@ -675,9 +702,9 @@ static int pass_variants(const Handle* h, int p, const PassArgs* pa = nullptr) {
         case 6: return 3;
         case 0: return x_fast_variants(h->Px, false, true);
         case 1: return y_fast_variants(h->Py, true);
-        case 2: {   // 0-2 FFT forms, 3 direct (fast_zd.cu), 4 split pencils (fast_zs.cu)
+        case 2: {   // 0-2 FFT forms, 3 direct (fast_zd.cu), 4 and 5 split pencils (fast_zs.cu)
             if (z_fast_variants(h->Pz, true) == 0) return 0;
-            if (h->Pz == 32 || h->Pz == 48) return 5;
+            if (h->Pz == 32 || h->Pz == 48) return 6;
             return z_direct_ok(h) ? 4 : 3;
         }
         case 3: return y_fast_variants(h->Py, true);

@@ -16,7 +16,8 @@
 // is flexible GMRES (the preconditioned vectors Z_k are kept). Arnoldi uses
 // classical Gram-Schmidt applied twice (CGS2) in FP64: each pass is one
 // batched dot-product kernel over the basis and one linear-combination kernel.
-// Givens rotations and the small least-squares solves run on the host.
+// Givens rotations and the small least-squares solves run on the device (one thread per
+// right-hand side); the host reads only the count of unconverged right-hand sides per step.
 // Batching: every (frequency, port) pair is an item; one FGMRES runs all items
 // in lock-step with batched operator products (per-item omega: the spectra do
 // not depend on it), batched Arnoldi kernels and one AMG hierarchy per frequency.
@@ -112,7 +113,8 @@ __global__ void k_dots_reduce(const double2* __restrict__ partial, int nblk, int
 
 // out[r][n] = beta * out[r][n] + sum_i coef[r][i] * V[r][i][n]
 __global__ void k_lincomb(double2* __restrict__ out, int64_t rstride_o, const double2* __restrict__ V, int64_t ldv,
-                          int64_t rstride_v, const double2* __restrict__ coef, int ldc, int nv, double beta, int64_t n) {
+                          int64_t rstride_v, const double2* __restrict__ coef, int ldc, int nv, double beta, int64_t n,
+                          double csign = 1.0) {
     const int r = blockIdx.y;
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= n) return;
@@ -123,7 +125,9 @@ __global__ void k_lincomb(double2* __restrict__ out, int64_t rstride_o, const do
     acc.y *= beta;
     for (int i = 0; i < nv; ++i) {
         const double2 a = Vr[(int64_t)i * ldv + idx];
-        const double2 k = c[i];
+        double2 k = c[i];
+        k.x *= csign;
+        k.y *= csign;
         acc.x += k.x * a.x - k.y * a.y;
         acc.y += k.x * a.y + k.y * a.x;
     }
@@ -228,6 +232,78 @@ __global__ void k_prec_post_node(const double2* __restrict__ v, double2* __restr
     out[(int64_t)r * Nvec + 5 * K + m] = id >= 0 ? b[(int64_t)r * nf + id] : v[(int64_t)r * Nvec + 5 * K + m];
 }
 
+// ------------------------------------------------------------------ Arnoldi bookkeeping on the device
+// One thread per right-hand side r (nb <= a few hundred). H is column-major per r,
+// H[r][i + k (m + 1)]; cs, sn [r][m]; g [r][m + 1]. Complex arithmetic in double2.
+__device__ __forceinline__ double2 zmul(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ __forceinline__ double2 zconj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ double2 zadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 zsub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double zabs(double2 a) { return hypot(a.x, a.y); }
+__device__ __forceinline__ double2 zscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+
+// Column k of the Hessenberg matrix from the two Gram-Schmidt passes (h1 + h2, and the norm of
+// the new vector below the diagonal), the earlier rotations applied to it, a new rotation that
+// zeroes its sub-diagonal entry, the rotated right-hand side g, the scale 1/||w|| of the next
+// basis vector, and the count of right-hand sides still above their tolerance (*active).
+__global__ void k_arnoldi_givens(double2* __restrict__ H, double2* __restrict__ cs, double2* __restrict__ sn,
+                                 double2* __restrict__ g, const double2* __restrict__ h1, const double2* __restrict__ h2,
+                                 const double2* __restrict__ hn2, int k, int m, int nb, const double* __restrict__ tol,
+                                 const double* __restrict__ beta0, const int* __restrict__ done, double* __restrict__ scl,
+                                 int* __restrict__ active) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nb) return;
+    double2* Hr = H + (size_t)r * (m + 1) * m + (size_t)k * (m + 1);
+    const double hn = sqrt(fmax(hn2[r].x, 0.0));
+    for (int i = 0; i <= k; ++i) Hr[i] = zadd(h1[(size_t)r * (k + 1) + i], h2[(size_t)r * (k + 1) + i]);
+    Hr[k + 1] = make_double2(hn, 0.0);
+    scl[r] = hn > 1e-300 * fmax(1.0, beta0[r]) ? 1.0 / hn : 0.0;
+    const double2* csr = cs + (size_t)r * m;
+    const double2* snr = sn + (size_t)r * m;
+    for (int i = 0; i < k; ++i) {
+        const double2 a = Hr[i], b = Hr[i + 1];
+        Hr[i] = zadd(zmul(csr[i], a), zmul(snr[i], b));
+        Hr[i + 1] = zsub(zmul(zconj(csr[i]), b), zmul(zconj(snr[i]), a));
+    }
+    // rotation [c s; -conj(s) conj(c)] with c = |a| / t, s = (a / |a|) conj(b) / t, t = hypot(|a|, |b|)
+    const double2 a = Hr[k], b = Hr[k + 1];
+    double2 c, sv;
+    const double na = zabs(a), nbv = zabs(b);
+    if (nbv == 0) { c = make_double2(1, 0); sv = make_double2(0, 0); }
+    else if (na == 0) { c = make_double2(0, 0); sv = zscale(zconj(b), 1.0 / nbv); }
+    else {
+        const double t = hypot(na, nbv);
+        c = make_double2(na / t, 0);
+        sv = zscale(zmul(zscale(a, 1.0 / na), zconj(b)), 1.0 / t);
+    }
+    cs[(size_t)r * m + k] = c;
+    sn[(size_t)r * m + k] = sv;
+    Hr[k] = zadd(zmul(c, a), zmul(sv, b));
+    Hr[k + 1] = make_double2(0, 0);
+    double2* gr = g + (size_t)r * (m + 1);
+    const double2 gk = gr[k];
+    gr[k + 1] = zscale(zmul(zconj(sv), gk), -1.0);
+    gr[k] = zmul(c, gk);
+    if (!(done[r] || zabs(gr[k + 1]) <= tol[r] * beta0[r])) atomicAdd(active, 1);
+}
+
+// y from the upper-triangular system H[0..kk) y = g (zero for converged right-hand sides)
+__global__ void k_arnoldi_backsolve(const double2* __restrict__ H, const double2* __restrict__ g, double2* __restrict__ y,
+                                    int kk, int m, int nb, const int* __restrict__ done) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nb) return;
+    const double2* Hr = H + (size_t)r * (m + 1) * m;
+    const double2* gr = g + (size_t)r * (m + 1);
+    double2* yr = y + (size_t)r * kk;
+    for (int i = kk - 1; i >= 0; --i) {
+        double2 t = done[r] ? make_double2(0, 0) : gr[i];
+        for (int j = i + 1; j < kk; ++j) t = zsub(t, zmul(Hr[i + (size_t)j * (m + 1)], yr[j]));
+        const double2 d = Hr[i + (size_t)i * (m + 1)];
+        const double dd = d.x * d.x + d.y * d.y;
+        yr[i] = dd > 0 && !done[r] ? zscale(zmul(t, zconj(d)), 1.0 / dd) : make_double2(0, 0);
+    }
+}
+
 // ------------------------------------------------------------------ host driver
 // Krylov storage: V[i][r][n] (i <= m) and Z[i][r][n] (i < m), so basis vector i
 // of all nb right-hand sides is one contiguous nb x N block that the batched
@@ -239,10 +315,19 @@ struct SolveWork {
     int64_t N = 0;
     int nf = 0;
     DevBuf X, B, R, W, D, V, Z, T32a, T32b, part, hbuf, E, Bs, Yd, freeid, freenodes, scl, om;
+    // Arnoldi bookkeeping on the device: Hessenberg columns, rotations, rotated right-hand
+    // sides, the two Gram-Schmidt coefficient sets, ||w||^2, the least-squares solution,
+    // per-right-hand-side tolerance, initial norm, converged flag and the active counts
+    DevBuf Hh, Hcs, Hsn, Hg, Hh1, Hh2, Hn, Hy, Htol, Hb0, Hdone, Hact;
+    int* pin = nullptr;                 // pinned host copies of the active count (two slots)
+    cudaEvent_t ev[2] = {nullptr, nullptr};
     ~SolveWork() {
         for (DevBuf* b : {&X, &B, &R, &W, &D, &V, &Z, &T32a, &T32b, &part, &hbuf, &E, &Bs, &Yd, &freeid, &freenodes,
-                          &scl, &om})
+                          &scl, &om, &Hh, &Hcs, &Hsn, &Hg, &Hh1, &Hh2, &Hn, &Hy, &Htol, &Hb0, &Hdone, &Hact})
             dev_free(*b);
+        if (pin) cudaFreeHost(pin);
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
     }
 };
 
@@ -250,27 +335,20 @@ static unsigned blocks_for(int64_t n, int t = 256) { return (unsigned)((n + t - 
 
 static int nblk_dots(int64_t N) { return (int)((N + DOT_THREADS * DOT_PER_THREAD - 1) / (DOT_THREADS * DOT_PER_THREAD)); }
 
-// h[r][i] = V_i^H w_r for i < nv (w = s.W)
-static int dots(Handle* h, SolveWork& s, const double2* Vb, int nv, const double2* w, std::vector<cdbl>& out) {
+// out[r][i] = V_i^H w_r for i < nv, left on the device (no synchronisation)
+static void dots_dev(Handle* h, SolveWork& s, const double2* Vb, int64_t ldv, int nv, const double2* w, double2* out) {
     const int64_t N = s.N;
     const int nblk = nblk_dots(N);
-    k_dots<<<dim3(nblk, s.nb), DOT_THREADS, 0, h->stream>>>(Vb, (int64_t)s.nb * N, N, w, N, nv, N,
-                                                            static_cast<double2*>(s.part.p), nblk);
-    k_dots_reduce<<<dim3(nv, s.nb), 256, 0, h->stream>>>(static_cast<double2*>(s.part.p), nblk, nv,
-                                                         static_cast<double2*>(s.hbuf.p));
-    out.resize((size_t)s.nb * nv);
-    SVH_CUDA_TRY(h, cudaMemcpyAsync(out.data(), s.hbuf.p, out.size() * 16, cudaMemcpyDeviceToHost, h->stream));
-    SVH_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
-    return SVH_OK;
+    k_dots<<<dim3(nblk, s.nb), DOT_THREADS, 0, h->stream>>>(Vb, ldv, N, w, N, nv, N, static_cast<double2*>(s.part.p),
+                                                            nblk);
+    k_dots_reduce<<<dim3(nv, s.nb), 256, 0, h->stream>>>(static_cast<double2*>(s.part.p), nblk, nv, out);
 }
 
-// out_r = beta * out_r + sum_i coef[r][i] * Vb_i,r
-static int lincomb(Handle* h, SolveWork& s, double2* out, const double2* Vb, int nv, const std::vector<cdbl>& coef,
-                   double beta) {
-    SVH_CUDA_TRY(h, cudaMemcpyAsync(s.hbuf.p, coef.data(), coef.size() * 16, cudaMemcpyHostToDevice, h->stream));
-    k_lincomb<<<dim3(blocks_for(s.N), s.nb), 256, 0, h->stream>>>(out, s.N, Vb, (int64_t)s.nb * s.N, s.N,
-                                                                   static_cast<double2*>(s.hbuf.p), nv, nv, beta, s.N);
-    return SVH_OK;
+// out_r = beta * out_r + sign * sum_i coef[r][i] * Vb_i,r with the coefficients on the device
+static void lincomb_dev(Handle* h, SolveWork& s, double2* out, const double2* Vb, int nv, const double2* coef,
+                        double beta, double sign) {
+    k_lincomb<<<dim3(blocks_for(s.N), s.nb), 256, 0, h->stream>>>(out, s.N, Vb, (int64_t)s.nb * s.N, s.N, coef, nv, nv,
+                                                                   beta, s.N, sign);
 }
 
 static int norms(Handle* h, SolveWork& s, const double2* w, std::vector<double>& out) {
@@ -330,16 +408,13 @@ static int apply_op(Handle* h, SolveWork& s, double omega, const double2* x, dou
     return SVH_OK;
 }
 
-static void givens(cdbl a, cdbl b, cdbl& c, cdbl& sn) {
-    if (std::abs(b) == 0) { c = 1; sn = 0; return; }
-    if (std::abs(a) == 0) { c = 0; sn = std::conj(b) / std::abs(b); return; }
-    const double t = std::hypot(std::abs(a), std::abs(b));
-    c = std::abs(a) / t;
-    sn = (a / std::abs(a)) * std::conj(b) / t;
-}
-
 // Flexible GMRES(m) for Kt D = R with right preconditioning; D in s.D.
 // Stops right-hand side r when its estimated residual is <= tol[r] * ||R_r||.
+// Each Arnoldi step runs entirely on the device: preconditioner, product, two Gram-Schmidt
+// passes, the norm, the Hessenberg column with its Givens rotation and the rotated residual
+// (k_arnoldi_givens); per step the host reads one int, how many right-hand sides are still
+// above their tolerance (a pinned copy behind an event), to stop the cycle. The restart's
+// small least-squares solve is k_arnoldi_backsolve.
 static int fgmres(Handle* h, SolveWork& s, double omega, int prec, const std::vector<double>& tol, int maxit,
                   int& iters_out) {
     const int nb = s.nb, m = s.m;
@@ -349,17 +424,26 @@ static int fgmres(Handle* h, SolveWork& s, double omega, int prec, const std::ve
     double2* W = static_cast<double2*>(s.W.p);
     double2* Dd = static_cast<double2*>(s.D.p);
     double2* Rr = static_cast<double2*>(s.R.p);
+    double2* Hh = static_cast<double2*>(s.Hh.p);
+    double2* Hg = static_cast<double2*>(s.Hg.p);
+    double2* h1 = static_cast<double2*>(s.Hh1.p);
+    double2* h2 = static_cast<double2*>(s.Hh2.p);
+    double2* hn = static_cast<double2*>(s.Hn.p);
+    int* act = static_cast<int*>(s.Hact.p);
+    const unsigned tb = 128, nbk = (unsigned)((nb + tb - 1) / tb);
     SVH_CUDA_TRY(h, cudaMemsetAsync(Dd, 0, (size_t)blk * 16, h->stream));
     std::vector<double> beta0;
     int rc = norms(h, s, Rr, beta0);
     if (rc) return rc;
+    SVH_CUDA_TRY(h, cudaMemcpyAsync(s.Htol.p, tol.data(), (size_t)nb * 8, cudaMemcpyHostToDevice, h->stream));
+    SVH_CUDA_TRY(h, cudaMemcpyAsync(s.Hb0.p, beta0.data(), (size_t)nb * 8, cudaMemcpyHostToDevice, h->stream));
     // V_0 slot temporarily holds the current residual
     SVH_CUDA_TRY(h, cudaMemcpyAsync(V, Rr, (size_t)blk * 16, cudaMemcpyDeviceToDevice, h->stream));
     int it = 0;
     while (true) {
         std::vector<double> beta;
         if ((rc = norms(h, s, V, beta))) return rc;
-        std::vector<bool> done(nb);
+        std::vector<int> done(nb);
         bool all = true;
         for (int r = 0; r < nb; ++r) {
             done[r] = beta[r] <= tol[r] * beta0[r] || beta0[r] == 0;
@@ -368,72 +452,46 @@ static int fgmres(Handle* h, SolveWork& s, double omega, int prec, const std::ve
         if (all || it >= maxit) break;
         std::vector<double> inv(nb);
         for (int r = 0; r < nb; ++r) inv[r] = beta[r] > 0 ? 1.0 / beta[r] : 0.0;
+        std::vector<cdbl> g0((size_t)nb * (m + 1), 0.0);
+        for (int r = 0; r < nb; ++r) g0[(size_t)r * (m + 1)] = beta[r];
         SVH_CUDA_TRY(h, cudaMemcpyAsync(s.scl.p, inv.data(), nb * 8, cudaMemcpyHostToDevice, h->stream));
+        SVH_CUDA_TRY(h, cudaMemcpyAsync(s.Hdone.p, done.data(), nb * 4, cudaMemcpyHostToDevice, h->stream));
+        SVH_CUDA_TRY(h, cudaMemcpyAsync(Hg, g0.data(), g0.size() * 16, cudaMemcpyHostToDevice, h->stream));
         k_scale<<<dim3(blocks_for(N), nb), 256, 0, h->stream>>>(V, N, V, N, static_cast<double*>(s.scl.p), N);
-        std::vector<cdbl> H((size_t)nb * (m + 1) * m, 0.0), cs((size_t)nb * m), sn((size_t)nb * m),
-            g((size_t)nb * (m + 1), 0.0);
-        for (int r = 0; r < nb; ++r) g[(size_t)r * (m + 1)] = beta[r];
         int kk = 0;
         for (int k = 0; k < m && it < maxit; ++k) {
             double2* Vk = V + k * blk;
             double2* Zk = Z + k * blk;
             if ((rc = apply_precond(h, s, Vk, Zk))) return rc;
             if ((rc = apply_op(h, s, omega, Zk, W, prec))) return rc;
-            // classical Gram-Schmidt, twice
-            std::vector<cdbl> h1, h2;
-            if ((rc = dots(h, s, V, k + 1, W, h1))) return rc;
-            std::vector<cdbl> neg(h1.size());
-            for (size_t i = 0; i < h1.size(); ++i) neg[i] = -h1[i];
-            if ((rc = lincomb(h, s, W, V, k + 1, neg, 1.0))) return rc;
-            if ((rc = dots(h, s, V, k + 1, W, h2))) return rc;
-            for (size_t i = 0; i < h2.size(); ++i) neg[i] = -h2[i];
-            if ((rc = lincomb(h, s, W, V, k + 1, neg, 1.0))) return rc;
-            std::vector<double> hn;
-            if ((rc = norms(h, s, W, hn))) return rc;
-            for (int r = 0; r < nb; ++r) inv[r] = hn[r] > 1e-300 * std::max(1.0, beta0[r]) ? 1.0 / hn[r] : 0.0;
-            SVH_CUDA_TRY(h, cudaMemcpyAsync(s.scl.p, inv.data(), nb * 8, cudaMemcpyHostToDevice, h->stream));
+            // classical Gram-Schmidt, twice, with the coefficients kept on the device
+            dots_dev(h, s, V, blk, k + 1, W, h1);
+            lincomb_dev(h, s, W, V, k + 1, h1, 1.0, -1.0);
+            dots_dev(h, s, V, blk, k + 1, W, h2);
+            lincomb_dev(h, s, W, V, k + 1, h2, 1.0, -1.0);
+            dots_dev(h, s, W, N, 1, W, hn);
+            SVH_CUDA_TRY(h, cudaMemsetAsync(act + (k & 1), 0, sizeof(int), h->stream));
+            k_arnoldi_givens<<<nbk, tb, 0, h->stream>>>(Hh, static_cast<double2*>(s.Hcs.p),
+                                                        static_cast<double2*>(s.Hsn.p), Hg, h1, h2, hn, k, m, nb,
+                                                        static_cast<double*>(s.Htol.p), static_cast<double*>(s.Hb0.p),
+                                                        static_cast<int*>(s.Hdone.p), static_cast<double*>(s.scl.p),
+                                                        act + (k & 1));
             k_scale<<<dim3(blocks_for(N), nb), 256, 0, h->stream>>>(V + (k + 1) * blk, N, W, N,
                                                                     static_cast<double*>(s.scl.p), N);
+            SVH_CUDA_TRY(h, cudaMemcpyAsync(s.pin + (k & 1), act + (k & 1), sizeof(int), cudaMemcpyDeviceToHost,
+                                            h->stream));
+            SVH_CUDA_TRY(h, cudaEventRecord(s.ev[k & 1], h->stream));
             ++it;
             kk = k + 1;
-            bool allc = true;
-            for (int r = 0; r < nb; ++r) {
-                cdbl* Hr = H.data() + (size_t)r * (m + 1) * m;   // column-major: Hr[i + k*(m+1)]
-                for (int i = 0; i <= k; ++i) Hr[i + (size_t)k * (m + 1)] = h1[(size_t)r * (k + 1) + i] + h2[(size_t)r * (k + 1) + i];
-                Hr[k + 1 + (size_t)k * (m + 1)] = hn[r];
-                cdbl* csr = cs.data() + (size_t)r * m;
-                cdbl* snr = sn.data() + (size_t)r * m;
-                for (int i = 0; i < k; ++i) {
-                    const cdbl a = Hr[i + (size_t)k * (m + 1)], b = Hr[i + 1 + (size_t)k * (m + 1)];
-                    Hr[i + (size_t)k * (m + 1)] = csr[i] * a + snr[i] * b;
-                    Hr[i + 1 + (size_t)k * (m + 1)] = -std::conj(snr[i]) * a + std::conj(csr[i]) * b;
-                }
-                givens(Hr[k + (size_t)k * (m + 1)], Hr[k + 1 + (size_t)k * (m + 1)], csr[k], snr[k]);
-                const cdbl a = Hr[k + (size_t)k * (m + 1)], b = Hr[k + 1 + (size_t)k * (m + 1)];
-                Hr[k + (size_t)k * (m + 1)] = csr[k] * a + snr[k] * b;
-                Hr[k + 1 + (size_t)k * (m + 1)] = 0;
-                cdbl* gr = g.data() + (size_t)r * (m + 1);
-                gr[k + 1] = -std::conj(snr[k]) * gr[k];
-                gr[k] = csr[k] * gr[k];
-                if (!(done[r] || std::abs(gr[k + 1]) <= tol[r] * beta0[r])) allc = false;
-            }
-            if (allc) break;
+            // the one value the host reads per step: how many right-hand sides are still above
+            // their tolerance (a step costs a preconditioner apply, far longer than this wait)
+            SVH_CUDA_TRY(h, cudaEventSynchronize(s.ev[k & 1]));
+            if (s.pin[k & 1] == 0) break;
         }
         // y from the triangular systems; D += sum_i y_i Z_i
-        std::vector<cdbl> y((size_t)nb * kk, 0.0);
-        for (int r = 0; r < nb; ++r) {
-            if (done[r]) continue;
-            const cdbl* Hr = H.data() + (size_t)r * (m + 1) * m;
-            const cdbl* gr = g.data() + (size_t)r * (m + 1);
-            cdbl* yr = y.data() + (size_t)r * kk;
-            for (int i = kk - 1; i >= 0; --i) {
-                cdbl t = gr[i];
-                for (int j = i + 1; j < kk; ++j) t -= Hr[i + (size_t)j * (m + 1)] * yr[j];
-                const cdbl d = Hr[i + (size_t)i * (m + 1)];
-                yr[i] = std::abs(d) > 0 ? t / d : 0.0;
-            }
-        }
-        if ((rc = lincomb(h, s, Dd, Z, kk, y, 1.0))) return rc;
+        k_arnoldi_backsolve<<<nbk, tb, 0, h->stream>>>(Hh, Hg, static_cast<double2*>(s.Hy.p), kk, m, nb,
+                                                       static_cast<int*>(s.Hdone.p));
+        lincomb_dev(h, s, Dd, Z, kk, static_cast<double2*>(s.Hy.p), 1.0, 1.0);
         // residual of the correction problem for the restart: V_0 <- R - Kt D
         if ((rc = apply_op(h, s, omega, Dd, W, prec))) return rc;
         SVH_CUDA_TRY(h, cudaMemcpyAsync(V, Rr, (size_t)blk * 16, cudaMemcpyDeviceToDevice, h->stream));
@@ -455,8 +513,16 @@ static int alloc_work(Handle* h, SolveWork& s, int nb, int m) {
         (rc = dev_alloc(h, s.V, (size_t)(m + 1) * blk * 16)) || (rc = dev_alloc(h, s.Z, (size_t)m * blk * 16)) ||
         (rc = dev_alloc(h, s.T32a, blk * 8)) || (rc = dev_alloc(h, s.T32b, blk * 8)) ||
         (rc = dev_alloc(h, s.part, (size_t)nblk_dots(s.N) * nb * (m + 1) * 16)) ||
-        (rc = dev_alloc(h, s.hbuf, (size_t)nb * (m + 1) * 16)) || (rc = dev_alloc(h, s.scl, (size_t)nb * 8)))
+        (rc = dev_alloc(h, s.hbuf, (size_t)nb * (m + 1) * 16)) || (rc = dev_alloc(h, s.scl, (size_t)nb * 8)) ||
+        (rc = dev_alloc(h, s.Hh, (size_t)nb * (m + 1) * m * 16)) || (rc = dev_alloc(h, s.Hcs, (size_t)nb * m * 16)) ||
+        (rc = dev_alloc(h, s.Hsn, (size_t)nb * m * 16)) || (rc = dev_alloc(h, s.Hg, (size_t)nb * (m + 1) * 16)) ||
+        (rc = dev_alloc(h, s.Hh1, (size_t)nb * (m + 1) * 16)) || (rc = dev_alloc(h, s.Hh2, (size_t)nb * (m + 1) * 16)) ||
+        (rc = dev_alloc(h, s.Hn, (size_t)nb * 16)) || (rc = dev_alloc(h, s.Hy, (size_t)nb * m * 16)) ||
+        (rc = dev_alloc(h, s.Htol, (size_t)nb * 8)) || (rc = dev_alloc(h, s.Hb0, (size_t)nb * 8)) ||
+        (rc = dev_alloc(h, s.Hdone, (size_t)nb * 4)) || (rc = dev_alloc(h, s.Hact, 2 * sizeof(int))))
         return rc;
+    SVH_CUDA_TRY(h, cudaHostAlloc(reinterpret_cast<void**>(&s.pin), 2 * sizeof(int), cudaHostAllocDefault));
+    for (cudaEvent_t& e : s.ev) SVH_CUDA_TRY(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     return SVH_OK;
 }
 

@@ -535,12 +535,17 @@ int svh_destroy(svh_handle* hh) {
     if (!h) return SVH_ERR_ARG;
     cudaSetDevice(h->device);
     cudaStreamSynchronize(h->stream);
-    if (h->aux) {
-        cudaStreamSynchronize(h->aux);
-        cudaStreamDestroy(h->aux);
-    }
+    for (cudaStream_t st : {h->aux, h->cpy_in, h->cpy_out})
+        if (st) {
+            cudaStreamSynchronize(st);
+            cudaStreamDestroy(st);
+        }
     for (cudaEvent_t e : {h->ev_fork, h->ev_spec, h->ev_done, h->ev_x})
         if (e) cudaEventDestroy(e);
+    for (int j = 0; j < kHostChunks; ++j) {
+        if (h->ev_in[j]) cudaEventDestroy(h->ev_in[j]);
+        if (h->ev_out[j]) cudaEventDestroy(h->ev_out[j]);
+    }
     free_all(h);
     if (h->tsvd) tsvd_free(h->tsvd);
     delete h;
@@ -926,19 +931,57 @@ int svh_matvec_host(svh_handle* hh, double omega, int nb, const void* x, void* y
     if (!x || !y || nb <= 0 || (precision != SVH_FP32 && precision != SVH_FP64))
         return set_err(h, SVH_ERR_ARG, "svh_matvec_host: bad arguments");
     if (!h->have_grid) return set_err(h, SVH_ERR_STATE, "svh_matvec_host: no grid");
-    const size_t bytes = (size_t)nb * (5 * h->K + h->M) * (precision == SVH_FP32 ? 8 : 16);
+    if (!h->have_kernels) return set_err(h, SVH_ERR_STATE, "svh_matvec_host: grid and kernels must be set up first");
+    if (!(omega > 0) || !std::isfinite(omega)) return set_err(h, SVH_ERR_ARG, "svh_matvec_host: omega must be > 0");
+    const size_t item = (size_t)(5 * h->K + h->M) * (precision == SVH_FP32 ? 8 : 16);
+    const size_t bytes = (size_t)nb * item;
     int rc;
     if (h->d_xin.bytes < bytes && (rc = dev_alloc(h, h->d_xin, bytes))) return rc;
     if (h->d_yout.bytes < bytes && (rc = dev_alloc(h, h->d_yout, bytes))) return rc;
-    // fork the product's second stream first: the Tucker restore overlaps the input copy
-    if ((rc = matvec_prefork(h))) return rc;
-    SVH_CUDA_TRY(h, cudaMemcpyAsync(h->d_xin.p, x, bytes, cudaMemcpyHostToDevice, h->stream));
-    if ((rc = matvec_mark_input_ready(h))) { h->preforked = false; return rc; }
-    rc = svh_matvec(hh, omega, nb, h->d_xin.p, h->d_yout.p, precision);
-    h->preforked = false;   // consumed by the product (or left over by a rejected call)
+    // The items go in up to kHostChunks chunks: every chunk is copied in on cpy_in as early as
+    // the link allows, multiplied on the handle's stream once its copy has landed, and copied out
+    // on cpy_out while the next chunk is multiplied, so only the first chunk's input copy and the
+    // last chunk's output copy add to the product's time. The first chunk's product runs the
+    // Tucker restore (rebuild mode), forked before its input copy so that the two overlap; the
+    // later chunks reuse the restored kernels.
+    const int nch = std::min(nb, kHostChunks);
+    char* xd = static_cast<char*>(h->d_xin.p);
+    char* yd = static_cast<char*>(h->d_yout.p);
+    const char* xh = static_cast<const char*>(x);
+    char* yh = static_cast<char*>(y);
+    if ((rc = matvec_prefork(h))) return rc;   // creates the copy streams too
+    SVH_CUDA_TRY(h, cudaEventRecord(h->ev_in[0], h->stream));   // the caller's earlier work on the stream
+    SVH_CUDA_TRY(h, cudaStreamWaitEvent(h->cpy_in, h->ev_in[0], 0));
+    int first[kHostChunks + 1];
+    for (int j = 0; j <= nch; ++j) first[j] = (int)((int64_t)nb * j / nch);
+    for (int j = 0; j < nch; ++j) {
+        const size_t off = (size_t)first[j] * item, len = (size_t)(first[j + 1] - first[j]) * item;
+        SVH_CUDA_TRY(h, cudaMemcpyAsync(xd + off, xh + off, len, cudaMemcpyHostToDevice, h->cpy_in));
+        SVH_CUDA_TRY(h, cudaEventRecord(h->ev_in[j], h->cpy_in));
+    }
+    for (int j = 0; j < nch && !rc; ++j) {
+        const size_t off = (size_t)first[j] * item, len = (size_t)(first[j + 1] - first[j]) * item;
+        const int nbj = first[j + 1] - first[j];
+        SVH_CUDA_TRY(h, cudaStreamWaitEvent(h->stream, h->ev_in[j], 0));
+        if (j == 0) {
+            if ((rc = matvec_mark_input_ready(h))) break;
+            rc = precision == SVH_FP32 ? launch_matvec32(h, omega, nbj, xd + off, yd + off, 0)
+                                       : launch_matvec64(h, omega, nbj, xd + off, yd + off, 0);
+        } else {
+            rc = launch_matvec_reuse(h, omega, nbj, xd + off, yd + off, precision);
+        }
+        if (rc) break;
+        SVH_CUDA_TRY(h, cudaEventRecord(h->ev_out[j], h->stream));
+        SVH_CUDA_TRY(h, cudaStreamWaitEvent(h->cpy_out, h->ev_out[j], 0));
+        SVH_CUDA_TRY(h, cudaMemcpyAsync(yh + off, yd + off, len, cudaMemcpyDeviceToHost, h->cpy_out));
+    }
+    h->preforked = false;   // consumed by the first product (or left over by a failed call)
+    cudaError_t e1 = cudaStreamSynchronize(h->cpy_in);
+    cudaError_t e2 = cudaStreamSynchronize(h->cpy_out);
+    cudaError_t e3 = cudaStreamSynchronize(h->stream);
     if (rc) return rc;
-    SVH_CUDA_TRY(h, cudaMemcpyAsync(y, h->d_yout.p, bytes, cudaMemcpyDeviceToHost, h->stream));
-    SVH_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess)
+        return cuda_err(h, e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : e3), "svh_matvec_host");
     return SVH_OK;
 }
 

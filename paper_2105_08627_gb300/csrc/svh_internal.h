@@ -97,6 +97,11 @@ struct Handle {
     // set by the host-buffer entry point: the second stream was forked before the input
     // copy (the restore overlaps it) and ev_x marks the input on the device
     bool preforked = false;
+    // copy streams of the host-buffer entry point: the items go in up to kHostChunks chunks,
+    // each copied in on cpy_in (ev_in), multiplied on the handle's stream (ev_out) and copied out
+    // on cpy_out while the next chunk is multiplied
+    cudaStream_t cpy_in = nullptr, cpy_out = nullptr;
+    cudaEvent_t ev_in[4] = {nullptr, nullptr, nullptr, nullptr}, ev_out[4] = {nullptr, nullptr, nullptr, nullptr};
 
     // ---- sparse preconditioner (amg.cpp), built per frequency by the solver
     void* precond = nullptr;
@@ -144,6 +149,9 @@ int matvec_prefork(Handle* h);
 // per handle at grid set-up, so that no product call creates them)
 int matvec_streams(Handle* h);
 int matvec_mark_input_ready(Handle* h);
+constexpr int kHostChunks = 4;
+// the product with the kernels that an earlier product of the same call prepared (no restore)
+int launch_matvec_reuse(Handle* h, double omega, int nb, const void* x, void* y, int precision);
 // FFT tile variants (matvec.cu)
 int autotune(Handle* h, int nb, int32_t* variants, double* ms);
 int set_pass_variant(Handle* h, int pass, int variant);

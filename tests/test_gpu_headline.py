@@ -66,14 +66,16 @@ def test_esfq512_bench_path_dense_input():
     check(h.matvec(om, xd), f"autotuned tiles {tiles.tolist()}")
     assert h.device_status() == 0
     counts, chosen = h.pass_variants()
-    for sched in range(counts[6]):                   # stream schedules (two item groups: 3)
+    for sched in range(counts[6]):                   # stream schedules
         h.set_pass_variant(6, sched)
         check(h.matvec(om, xd), f"schedule {sched}")
     h.set_pass_variant(6, int(chosen[6]))
-    for zv in range(counts[2]):                      # every z-pass form at Pz = 48
-        h.set_pass_variant(2, zv)
-        check(h.matvec(om, xd), f"z variant {zv}")
-        assert h.device_status() == 0
+    for p in (2, 1, 3, 0, 4):                        # every tile variant of every pass at this size
+        for v in range(counts[p]):
+            h.set_pass_variant(p, v)
+            check(h.matvec(om, xd), f"pass {p} variant {v}")
+            assert h.device_status() == 0
+        h.set_pass_variant(p, int(chosen[p]))
     h.close()
 
 
@@ -99,10 +101,11 @@ def test_meander256_bench_path_dense_input():
 
     check(f"autotuned tiles {tiles.tolist()}")
     counts, chosen = h.pass_variants()
-    for zv in range(counts[2]):                      # FFT forms and the direct z pass
-        h.set_pass_variant(2, zv)
-        check(f"z variant {zv}")
-    h.set_pass_variant(2, int(chosen[2]))
+    for p in (2, 1, 3, 0, 4):                        # every tile variant (z: FFT forms and the direct pass)
+        for v in range(counts[p]):
+            h.set_pass_variant(p, v)
+            check(f"pass {p} variant {v}")
+        h.set_pass_variant(p, int(chosen[p]))
     for sched in range(counts[6]):                   # stream schedules with the restore
         h.set_pass_variant(6, sched)
         check(f"schedule {sched}")

@@ -129,6 +129,33 @@ def test_meander_256x256x8_solve_true_residual():
     h.close()
 
 
+def _stored_oracle_inductance(name):
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)
+    rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    return np.array([[float(v) for v in r] for r in rows])
+
+
+@pytest.mark.slow
+def test_meander256_inductance_vs_stored_oracle():
+    """cfg 2 port inductance from the library (device quadrature; FP32 products in FP64
+    refinement; resident spectra and the Tucker restore in every product at tol 1e-8) against
+    the oracle's own solve of the same structure (tests/golden/meander256_inductance.txt, written
+    by the committed script beside it from oracle/ alone): within 1e-6."""
+    from paper_2105_08627_gb300 import svh
+    Lref = _stored_oracle_inductance("meander256_inductance.txt")
+    s = S.meander_cfg2()
+    h = handle_for(s)
+    res = h.solve([s.freqs[0]])
+    assert res["stats"]["final_rre"] <= 1e-8
+    assert np.abs(res["L"][0] - Lref).max() <= L_TOL * np.abs(Lref).max(), (res["L"][0], Lref)
+    h.tucker_compress(1e-8)
+    h.set_kernel_mode(svh.SVH_KERNELS_TUCKER_REBUILD)
+    res = h.solve([s.freqs[0]])
+    assert np.abs(res["L"][0] - Lref).max() <= L_TOL * np.abs(Lref).max(), (res["L"][0], Lref)
+    h.close()
+
+
 def _schur(s, seed):
     """S = A_F diag(1/y) A_F^T on the free nodes of a structure (the Eq. 14
     operator), y_beta = s_beta (Eq. 16-18 scale) times a seeded factor within
