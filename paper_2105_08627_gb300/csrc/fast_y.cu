@@ -6,8 +6,8 @@
 //   2: the same split with 128 threads,
 //   3: the transposed split N2 x N1 with 256 threads (sizes where both
 //      factors suit the pruned first and second stages; elsewhere 3 runs 0),
-//   4: the cp.async-staged persistent kernel k_ycol_async, 8 kx columns per tile (sizes >= 256),
-//   5: the same with 4 kx columns per tile.
+//   4: the cp.async-staged persistent kernel k_ycol_async, 8 kx columns per tile (sizes >= 256;
+//      4-column tiles, more blocks per SM, measured slower).
 // FP64 has variant 0 only (128 threads).
 #include <algorithm>
 #include <type_traits>
@@ -58,10 +58,6 @@ static bool run_y_size(const PassArgs& a, cudaStream_t s) {
                 if constexpr (N1 * N2 >= 256 && N2 <= 64)
                     if (a.Px % 8 == 0) { run_y_async<N1, N2, INV, 8 * N2>(a, s); return true; }
                 break;
-            case 5:   // the same on 4-column tiles: a quarter of the shared memory, more blocks per SM
-                if constexpr (N1 * N2 >= 256 && N2 <= 64 && N2 >= 16)
-                    if (a.Px % 4 == 0) { run_y_async<N1, N2, INV, 4 * N2>(a, s); return true; }
-                break;
             default: break;
         }
         run_y<T, N1, N2, INV, 256>(a, s);
@@ -92,8 +88,8 @@ static bool dispatch_y(const PassArgs& a, cudaStream_t s) {
 
 int y_fast_variants(int Py, bool fp32) {
     if (!fp32) return 1;
-    switch (Py) {   // 4, 5: the cp.async-staged kernel (sizes >= 256; where 3 has no transposed split it runs 0)
-        case 256: case 384: case 512: case 768: case 1024: return 6;
+    switch (Py) {   // 4: the cp.async-staged kernel (sizes >= 256; where 3 has no transposed split it runs 0)
+        case 256: case 384: case 512: case 768: case 1024: return 5;
         case 32: case 128: return 4;
         case 16: case 48: case 64: case 96: case 192: return 3;
         default: return 0;

@@ -60,7 +60,7 @@ static void run_z(const PassArgs& a, cudaStream_t s) {
     if constexpr (std::is_same<T, float>::value) {
         if (a.var == 2 && a.zcontig && 2 * a.nza <= PZ && run_z_tma<PZ>(a, s)) return;
         if (a.var == 4 && launch_z_split(a, s)) return;   // 3 is the direct z pass (fast_zd.cu)
-        if (a.var == 5 && launch_z_split16(a, s)) return;
+        if ((a.var == 5 || a.var == 6) && launch_z_split16(a, s, a.var == 5)) return;
     }
     if (a.var != 1 && a.zcontig && 2 * a.nza <= PZ) {
         cudaFuncSetAttribute(k_zpass_half<T, PZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

@@ -99,17 +99,22 @@ __global__ void __launch_bounds__(320, 2) k_zpass_split(const __grid_constant__ 
     }
 }
 
-// Variant 5: the same split-pencil transform on tiles of TC kx columns (TC = 16: blocks of
-// 160 threads, half the shared memory, twice the blocks per SM), with the tile's spectra packed
-// per frequency point as two float4 (G00, Sx, Sy, Sz | Qx, Qy, Qz, 0): two 16-byte shared loads
-// per point instead of seven.
-template <int PZ, int TC>
-__global__ void __launch_bounds__(10 * TC, 4) k_zpass_split4(const __grid_constant__ PassArgs a) {
+// Variants 5 and 6: the same split-pencil transform on tiles of TC kx columns (TC = 16: blocks
+// of 160 threads, 44 KB of shared memory), with the tile's octant spectra packed per frequency
+// point as two float4 (G00, Sx, Sy, Sz | Qx, Qy, Qz, 0): two 16-byte shared loads per point
+// instead of seven.
+// PREF: the next item's inputs are loaded into registers while the current item is transformed
+// (4 blocks per SM); without it the loads come right before each item's transform and the
+// register budget allows 5 blocks per SM (variant 6), whose other warps cover the latency.
+template <int PZ, int TC, bool PREF>
+__global__ void __launch_bounds__(10 * TC, PREF ? 4 : 5) k_zpass_split4(const __grid_constant__ PassArgs a) {
     using C = float2;
     constexpr int NT = 10 * TC, H = PZ / 2, Q = H / 2, TS = 96 / PZ, NH = PZ / 2 + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C(*buf)[2][H][TC] = reinterpret_cast<C(*)[2][H][TC]>(smem_raw);   // [5][parity][k][column]
-    float4(*sp)[PZ][TC] = reinterpret_cast<float4(*)[PZ][TC]>(smem_raw + sizeof(C) * 5 * 2 * H * TC);  // [2][kz][col]
+    // octant spectra of the tile, az = 0 .. PZ / 2: frequency kz reads az = min(kz, PZ - kz), with
+    // S_z negated for kz > PZ / 2 (at kz = PZ / 2 itself the odd S_z spectrum vanishes)
+    float4(*sp)[NH][TC] = reinterpret_cast<float4(*)[NH][TC]>(smem_raw + sizeof(C) * 5 * 2 * H * TC);  // [2][az][col]
     const int q = threadIdx.x / TC, lane = threadIdx.x % TC;
     const int al = q >> 1, par = q & 1;
     const int kx0 = blockIdx.x * TC, ky = blockIdx.y, kx = kx0 + lane;
@@ -134,12 +139,9 @@ __global__ void __launch_bounds__(10 * TC, 4) k_zpass_split4(const __grid_consta
 #pragma unroll
             for (int az = 0; az < NH; ++az) val[az] = __ldg(spec + u * Sk + az * plane + off);
 #pragma unroll
-            for (int az = 0; az < NH; ++az) {
-                spf[((half * PZ + az) * TC + ln) * 4 + comp] = sg * val[az];
-                if (az > 0 && PZ - az != az) spf[((half * PZ + PZ - az) * TC + ln) * 4 + comp] = (u == 3 ? -sg : sg) * val[az];
-            }
+            for (int az = 0; az < NH; ++az) spf[((half * NH + az) * TC + ln) * 4 + comp] = sg * val[az];
         }
-        for (int i = threadIdx.x; i < PZ * TC; i += NT) spf[((PZ + i / TC) * TC + i % TC) * 4 + 3] = 0.f;
+        for (int i = threadIdx.x; i < NH * TC; i += NT) spf[((NH + i / TC) * TC + i % TC) * 4 + 3] = 0.f;
     }
     C* B2 = static_cast<C*>(a.B2);
     const int64_t plane = (int64_t)a.Py * a.Px;
@@ -157,12 +159,13 @@ __global__ void __launch_bounds__(10 * TC, 4) k_zpass_split4(const __grid_consta
             pre[m] = z;
         }
     };
-    fetch(0);
+    if (PREF) fetch(0);
     for (int b = 0; b < a.nb; ++b) {
         {
             C v[H];
+            if (!PREF) fetch(b);
             reg_fft_lowin<H, false>(pre, v);
-            if (b + 1 < a.nb) fetch(b + 1);
+            if (PREF && b + 1 < a.nb) fetch(b + 1);
             // a thread writes only its own (basis, parity, column) line here, which after the
             // previous item's second barrier only it reads: no barrier is needed before this
 #pragma unroll
@@ -178,9 +181,10 @@ __global__ void __launch_bounds__(10 * TC, 4) k_zpass_split4(const __grid_consta
                 lo[p] = cadd(e, o);
                 hi[p] = csub(e, o);
             }
-            const float4 l0 = sp[0][k][ln], l1 = sp[1][k][ln], h0 = sp[0][k + H][ln], h1 = sp[1][k + H][ln];
+            // k reads az = k; k + H (> PZ / 2 for k > 0) reads az = H - k with S_z negated
+            const float4 l0 = sp[0][k][ln], l1 = sp[1][k][ln], h0 = sp[0][H - k][ln], h1 = sp[1][H - k][ln];
             block_multiply5<float>(lo, l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z);
-            block_multiply5<float>(hi, h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z);
+            block_multiply5<float>(hi, h0.x, h0.y, h0.z, -h0.w, h1.x, h1.y, h1.z);
 #pragma unroll
             for (int p = 0; p < 5; ++p) {
                 buf[p][0][k][ln] = cadd(lo[p], hi[p]);
@@ -204,17 +208,17 @@ __global__ void __launch_bounds__(10 * TC, 4) k_zpass_split4(const __grid_consta
     }
 }
 
-template <int PZ, int TC>
+template <int PZ, int TC, bool PREF>
 static void run_zsplit4(const PassArgs& a, cudaStream_t s) {
-    const size_t sm = (size_t)5 * PZ * TC * sizeof(float2) + (size_t)2 * PZ * TC * sizeof(float4);
-    cudaFuncSetAttribute(k_zpass_split4<PZ, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_zpass_split4<PZ, TC><<<dim3((unsigned)((a.Px + TC - 1) / TC), (unsigned)a.Py), 10 * TC, sm, s>>>(a);
+    const size_t sm = (size_t)5 * PZ * TC * sizeof(float2) + (size_t)2 * (PZ / 2 + 1) * TC * sizeof(float4);
+    cudaFuncSetAttribute(k_zpass_split4<PZ, TC, PREF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_zpass_split4<PZ, TC, PREF><<<dim3((unsigned)((a.Px + TC - 1) / TC), (unsigned)a.Py), 10 * TC, sm, s>>>(a);
 }
 
-bool launch_z_split16(const PassArgs& a, cudaStream_t s) {
+bool launch_z_split16(const PassArgs& a, cudaStream_t s, bool prefetch) {
     if (!z_split_ok(a.Pz, a.nza, a.zcontig)) return false;
-    if (a.Pz == 32) run_zsplit4<32, 16>(a, s);
-    else run_zsplit4<48, 16>(a, s);
+    if (a.Pz == 32) prefetch ? run_zsplit4<32, 16, true>(a, s) : run_zsplit4<32, 16, false>(a, s);
+    else prefetch ? run_zsplit4<48, 16, true>(a, s) : run_zsplit4<48, 16, false>(a, s);
     return true;
 }
 

@@ -441,7 +441,7 @@ __global__ void __launch_bounds__(NT) k_ycol_fast(const __grid_constant__ PassAr
 // first stage has read the current tile from it, the copies of the block's NEXT tile are issued,
 // so they land while this tile is twiddled, exchanged, transformed and stored.
 template <int N1, int N2, bool INV, int NT>
-__global__ void __launch_bounds__(NT, NT <= 128 ? 4 : 2) k_ycol_async(const __grid_constant__ PassArgs a, int ntiles) {
+__global__ void __launch_bounds__(NT, 2) k_ycol_async(const __grid_constant__ PassArgs a, int ntiles) {
     using C = float2;
     constexpr int N = N1 * N2;
     constexpr int TB = NT / N2;                 // kx columns per tile (even)
@@ -857,7 +857,7 @@ bool launch_z_direct(const PassArgs& a, cudaStream_t s);
 // planes consecutive and in the lower half
 bool z_split_ok(int Pz, int nza, int zcontig);
 bool launch_z_split(const PassArgs& a, cudaStream_t s);
-bool launch_z_split16(const PassArgs& a, cudaStream_t s);
+bool launch_z_split16(const PassArgs& a, cudaStream_t s, bool prefetch);
 void launch_spec_to_zk(const float* S, float* R, const float* W, int Hx, int Hy, int Hz, int D, cudaStream_t s);
 bool z_fast_size(int Pz);
 // number of tile variants of a pass at this size (0: no specialised kernel)

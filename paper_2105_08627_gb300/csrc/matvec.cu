@@ -702,9 +702,9 @@ static int pass_variants(const Handle* h, int p, const PassArgs* pa = nullptr) {
         case 6: return 3;
         case 0: return x_fast_variants(h->Px, false, true);
         case 1: return y_fast_variants(h->Py, true);
-        case 2: {   // 0-2 FFT forms, 3 direct (fast_zd.cu), 4 and 5 split pencils (fast_zs.cu)
+        case 2: {   // 0-2 FFT forms, 3 direct (fast_zd.cu), 4-6 split pencils (fast_zs.cu)
             if (z_fast_variants(h->Pz, true) == 0) return 0;
-            if (h->Pz == 32 || h->Pz == 48) return 6;
+            if (h->Pz == 32 || h->Pz == 48) return 7;
             return z_direct_ok(h) ? 4 : 3;
         }
         case 3: return y_fast_variants(h->Py, true);
