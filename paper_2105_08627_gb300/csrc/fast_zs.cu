@@ -167,24 +167,26 @@ __global__ void __launch_bounds__(10 * TC, PREF ? 4 : 5) k_zpass_split4(const __
             reg_fft_lowin<H, false>(pre, v);
             if (PREF && b + 1 < a.nb) fetch(b + 1);
             // a thread writes only its own (basis, parity, column) line here, which after the
-            // previous item's second barrier only it reads: no barrier is needed before this
+            // previous item's second barrier only it reads: no barrier is needed before this (the
+            // odd line's twiddles W^k are applied by the block-product tasks)
 #pragma unroll
-            for (int k = 0; k < H; ++k) buf[al][par][k][lane] = (par && k) ? cmul(v[k], w96<C>(k * TS)) : v[k];
+            for (int k = 0; k < H; ++k) buf[al][par][k][lane] = v[k];
         }
         __syncthreads();
         for (int task = threadIdx.x; task < H * TC; task += NT) {
             const int k = task / TC, ln = task % TC;
+            const C w = w96<C>(k * TS);   // W^k of the odd-sample half (1 at k = 0)
             C lo[5], hi[5];
 #pragma unroll
             for (int p = 0; p < 5; ++p) {
-                const C e = buf[p][0][k][ln], o = buf[p][1][k][ln];
+                const C e = buf[p][0][k][ln], o = cmul(buf[p][1][k][ln], w);
                 lo[p] = cadd(e, o);
                 hi[p] = csub(e, o);
             }
             // k reads az = k; k + H (> PZ / 2 for k > 0) reads az = H - k with S_z negated
             const float4 l0 = sp[0][k][ln], l1 = sp[1][k][ln], h0 = sp[0][H - k][ln], h1 = sp[1][H - k][ln];
-            block_multiply5<float>(lo, l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z);
-            block_multiply5<float>(hi, h0.x, h0.y, h0.z, -h0.w, h1.x, h1.y, h1.z);
+            block_multiply5_fma(lo, l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z);
+            block_multiply5_fma(hi, h0.x, h0.y, h0.z, -h0.w, h1.x, h1.y, h1.z);
 #pragma unroll
             for (int p = 0; p < 5; ++p) {
                 buf[p][0][k][ln] = cadd(lo[p], hi[p]);

@@ -559,6 +559,37 @@ __device__ __forceinline__ void block_multiply5(typename CT<T>::type* io, T g, T
     io[0] = Yx; io[1] = Yy; io[2] = Yz; io[3] = Y2; io[4] = Y3;
 }
 
+// The same block product in scalar FP32 fused multiply-adds: the +-i factors become operand
+// swaps and signs, so each complex-by-real term is two FMAs and no moves
+__device__ __forceinline__ void block_multiply5_fma(float2* io, float g, float sx, float sy, float sz, float qx,
+                                                    float qy, float qz) {
+    const float2 Ix = io[0], Iy = io[1], Iz = io[2], I2 = io[3], I3 = io[4];
+    const float px = I2.x + I3.x, py = I2.y + I3.y;   // I2 + I3
+    const float mx = I3.x - I2.x, my = I3.y - I2.y;   // I3 - I2
+    const float s2 = 2.f * sz, qs = qx + qy, qd = qx - qy, q3 = qs + 4.f * qz;
+    float2 Y;
+    // Yx = g Ix - i sx (I2 + I3)
+    Y.x = fmaf(g, Ix.x, sx * py);
+    Y.y = fmaf(g, Ix.y, -sx * px);
+    io[0] = Y;
+    // Yy = g Iy - i sy (I3 - I2)
+    Y.x = fmaf(g, Iy.x, sy * my);
+    Y.y = fmaf(g, Iy.y, -sy * mx);
+    io[1] = Y;
+    // Yz = g Iz + i 2 sz I3
+    Y.x = fmaf(g, Iz.x, -s2 * I3.y);
+    Y.y = fmaf(g, Iz.y, s2 * I3.x);
+    io[2] = Y;
+    // Y2 = i sx Ix - i sy Iy + qs I2 + qd I3
+    Y.x = fmaf(qd, I3.x, fmaf(qs, I2.x, fmaf(sy, Iy.y, -sx * Ix.y)));
+    Y.y = fmaf(qd, I3.y, fmaf(qs, I2.y, fmaf(-sy, Iy.x, sx * Ix.x)));
+    io[3] = Y;
+    // Y3 = i sx Ix + i sy Iy - i 2 sz Iz + qd I2 + q3 I3
+    Y.x = fmaf(q3, I3.x, fmaf(qd, I2.x, fmaf(s2, Iz.y, fmaf(-sy, Iy.y, -sx * Ix.y))));
+    Y.y = fmaf(q3, I3.y, fmaf(qd, I2.y, fmaf(-s2, Iz.x, fmaf(sy, Iy.x, sx * Ix.x))));
+    io[4] = Y;
+}
+
 // Spectra of one z-pass tile (32 kx columns at one ky, all PZ planes) into
 // shared memory sp[u][kz][lane], with the odd S-kernel signs folded in: only
 // the octant |k| <= P/2 is stored, so kz and PZ - kz share the value at
