@@ -199,7 +199,7 @@ def pass_bytes(info, nb, csz, fused=False, zk_planes=0):
     Ht = info["Hx"] * info["Hy"] * info["Hz"]
     rows_line = 5 * nrows * Px * csz          # all active x-lines of one item, padded
     planes = 5 * nza * Py * Px * csz          # all active planes after the y transform
-    vidx = 4 * nrows * Kx
+    vidx = 8 * nrows + 4 * K                  # per active row: first voxel and count; per voxel: x
     if fused:
         return {
             "tucker_rebuild": 7 * Ht * 4,

@@ -35,6 +35,8 @@ struct PassArgs {
     const void* twz;
     const int32_t* vidx;     // [nza][Ky][Kx] voxel index or -1
     const int32_t* rows;     // active rows zi*Ky + y
+    const int2* rinfo;       // per active row: first voxel index, voxel count
+    const int32_t* vx;       // per voxel: x
     const uint8_t* rowmask;  // [nza][Ky]
     const int32_t* zlist;    // active planes
     const int32_t* node;     // [K][6]
@@ -135,26 +137,29 @@ __global__ void __launch_bounds__(NT) k_xrow(const __grid_constant__ PassArgs a)
         const int64_t line = line0 + l;
         C v[N1];
         if constexpr (!INV) {
-            // x < Kx <= N / 2: inputs n1 >= N1 / 2 are zero (input-pruned first stage)
-            C hv[N1 / 2];
+            // x < Kx <= N / 2: inputs n1 >= N1 / 2 are zero (input-pruned first stage). The row's
+            // voxels are one index range in x order: they are read contiguously (with their x)
+            // into the line's row in shared memory, then taken in the transform's order
+            C* lrow = buf + l * (N / 2);
 #pragma unroll
-            for (int n1 = 0; n1 < N1 / 2; ++n1) { hv[n1].x = 0; hv[n1].y = 0; }
+            for (int n1 = 0; n1 < N1 / 2; ++n1) {
+                lrow[n1 * N2 + n2].x = 0;
+                lrow[n1 * N2 + n2].y = 0;
+            }
+            __syncthreads();
             if (line < a.nlines) {
                 const int64_t ba = line / a.nrows;
-                const int row = a.rows[line - ba * a.nrows];
+                const int2 ri = a.rinfo[line - ba * a.nrows];
                 const int64_t b = ba / 5;
                 const int al = (int)(ba - 5 * b);
-                const C* xb = static_cast<const C*>(a.x) + b * a.Nvec + al * a.K;
-                const int32_t* vr = a.vidx + (int64_t)row * a.Kx;
-#pragma unroll
-                for (int n1 = 0; n1 < N1 / 2; ++n1) {
-                    const int n = n1 * N2 + n2;
-                    if (n < a.Kx) {
-                        const int vi = __ldg(vr + n);
-                        if (vi >= 0) hv[n1] = xb[vi];
-                    }
-                }
+                const C* xb = static_cast<const C*>(a.x) + b * a.Nvec + al * a.K + ri.x;
+                const int32_t* xr = a.vx + ri.x;
+                for (int j = n2; j < ri.y; j += N2) lrow[__ldg(xr + j)] = xb[j];
             }
+            __syncthreads();
+            C hv[N1 / 2];
+#pragma unroll
+            for (int n1 = 0; n1 < N1 / 2; ++n1) hv[n1] = lrow[n1 * N2 + n2];
             reg_fft_lowin<N1, false>(hv, v);
         } else {
             if (line < a.nlines) {
@@ -293,52 +298,54 @@ __global__ void __launch_bounds__(NT) k_xinv_grouped(const __grid_constant__ Pas
     }
     __syncthreads();
     const T inv_dx = (T)(1.0 / a.dx);
-    for (int task = threadIdx.x; task < G * Kx; task += NT) {
-        const int gl = task / Kx, x = task % Kx;
+    // one task per voxel of the block's rows (each row's voxels are one index range, in x order)
+    for (int gl = 0; gl < G; ++gl) {
         const int64_t g = g0 + gl;
-        if (g >= ngroups) continue;
+        if (g >= ngroups) break;
         const int64_t b = g / a.nrows;
-        const int row = a.rows[g - b * a.nrows];
-        const int vi = __ldg(a.vidx + (int64_t)row * Kx + x);
-        if (vi < 0) continue;
-        const double om = a.omegas ? a.omegas[b] : a.omega;
-        const T cs = a.omegas ? (T)(om * a.mu * a.dx * a.inv_P) : (T)a.conv_scale;
-        // two-fluid c = a + j omega mu b (Eq. 22-23), once per voxel
-        const T lm = (T)a.lam[vi], s0 = (T)a.sig0[vi];
-        const T wm = (T)(om * a.mu);
-        const T wml2 = wm * lm * lm;
-        const T tt = s0 * wml2;
-        const T den = (T)1 + tt * tt;
-        const T cre = s0 * wml2 * wml2 / den * inv_dx, cim = wm * (lm * lm / den) * inv_dx;
-        const C* xb = static_cast<const C*>(a.x) + b * a.Nvec;
-        C* yb = static_cast<C*>(a.y) + b * a.Nvec;
-        C ph[6];
-        const int32_t* nd = a.node + (int64_t)vi * 6;
-#pragma unroll
-        for (int f = 0; f < 6; ++f) {
-            const int m = nd[f];
-            if (!a.masked || a.freem[m]) ph[f] = xb[5 * a.K + m];
-            else { ph[f].x = 0; ph[f].y = 0; }
-        }
-#pragma unroll
-        for (int be = 0; be < 5; ++be) {
-            const C cv = buf[(gl * 5 + be) * LDX + x];
-            C val;
-            val.x = -cs * cv.y;
-            val.y = cs * cv.x;
-            const T sb = be < 3 ? (T)1 : (be == 3 ? (T)(1.0 / 6.0) : (T)0.5);
-            const C I = xb[be * a.K + vi];
-            val.x += sb * (cre * I.x - cim * I.y);
-            val.y += sb * (cre * I.y + cim * I.x);
+        const int2 ri = a.rinfo[g - b * a.nrows];
+        for (int j = threadIdx.x; j < ri.y; j += NT) {
+            const int vi = ri.x + j;
+            const int x = __ldg(a.vx + vi);
+            const double om = a.omegas ? a.omegas[b] : a.omega;
+            const T cs = a.omegas ? (T)(om * a.mu * a.dx * a.inv_P) : (T)a.conv_scale;
+            // two-fluid c = a + j omega mu b (Eq. 22-23), once per voxel
+            const T lm = (T)a.lam[vi], s0 = (T)a.sig0[vi];
+            const T wm = (T)(om * a.mu);
+            const T wml2 = wm * lm * lm;
+            const T tt = s0 * wml2;
+            const T den = (T)1 + tt * tt;
+            const T cre = s0 * wml2 * wml2 / den * inv_dx, cim = wm * (lm * lm / den) * inv_dx;
+            const C* xb = static_cast<const C*>(a.x) + b * a.Nvec;
+            C* yb = static_cast<C*>(a.y) + b * a.Nvec;
+            C ph[6];
+            const int32_t* nd = a.node + (int64_t)vi * 6;
 #pragma unroll
             for (int f = 0; f < 6; ++f) {
-                const float fl = face_flux(be, f);
-                if (fl != 0.f) {
-                    val.x -= (T)fl * ph[f].x;
-                    val.y -= (T)fl * ph[f].y;
-                }
+                const int m = nd[f];
+                if (!a.masked || a.freem[m]) ph[f] = xb[5 * a.K + m];
+                else { ph[f].x = 0; ph[f].y = 0; }
             }
-            yb[be * a.K + vi] = val;
+#pragma unroll
+            for (int be = 0; be < 5; ++be) {
+                const C cv = buf[(gl * 5 + be) * LDX + x];
+                C val;
+                val.x = -cs * cv.y;
+                val.y = cs * cv.x;
+                const T sb = be < 3 ? (T)1 : (be == 3 ? (T)(1.0 / 6.0) : (T)0.5);
+                const C I = xb[be * a.K + vi];
+                val.x += sb * (cre * I.x - cim * I.y);
+                val.y += sb * (cre * I.y + cim * I.x);
+#pragma unroll
+                for (int f = 0; f < 6; ++f) {
+                    const float fl = face_flux(be, f);
+                    if (fl != 0.f) {
+                        val.x -= (T)fl * ph[f].x;
+                        val.y -= (T)fl * ph[f].y;
+                    }
+                }
+                yb[be * a.K + vi] = val;
+            }
         }
     }
 }

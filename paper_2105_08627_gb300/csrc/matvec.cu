@@ -425,6 +425,8 @@ static PassArgs pass_args(Handle* h, double omega, const double* d_omegas, int n
     pa.x = x; pa.y = y; pa.B1 = B1; pa.B2 = B2; pa.spec = spec;
     pa.twx = twx; pa.twy = twy; pa.twz = twz;
     pa.vidx = vidx; pa.rows = rows; pa.rowmask = d_rowmask;
+    pa.rinfo = static_cast<const int2*>(h->d_rinfo.p);
+    pa.vx = static_cast<const int32_t*>(h->d_vx.p);
     pa.zlist = static_cast<const int32_t*>(h->d_zlist.p);
     pa.node = static_cast<const int32_t*>(h->d_node.p);
     pa.freem = static_cast<const uint8_t*>(h->d_free.p);

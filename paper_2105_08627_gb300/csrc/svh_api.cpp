@@ -136,7 +136,7 @@ static void free_all(Handle* h) {
     free_kernels(h);
     prof_release(h);
     precond_free(h);
-    for (DevBuf* b : {&h->d_vidx, &h->d_rows, &h->d_rowmask, &h->d_zlist, &h->d_node, &h->d_ninc,
+    for (DevBuf* b : {&h->d_vidx, &h->d_rows, &h->d_rinfo, &h->d_vx, &h->d_rowmask, &h->d_zlist, &h->d_node, &h->d_ninc,
                       &h->d_free, &h->d_lam, &h->d_sig0, &h->d_B1, &h->d_B2, &h->d_xin, &h->d_yout, &h->d_omegas,
                       &h->d_status})
         dev_free(*b);
@@ -664,6 +664,21 @@ int svh_setup_grid(svh_handle* hh, int Kx, int Ky, int Kz, double dx, const uint
         for (int y = 0; y < Ky; ++y)
             if (rowmask[(size_t)zi * Ky + y]) h->rows.push_back(zi * Ky + y);
     }
+    // voxels are numbered in cell order (x fastest): each active row's voxels are one range
+    std::vector<int32_t> rinfo(2 * h->rows.size()), vx(K);
+    for (size_t i = 0; i < h->rows.size(); ++i) {
+        const int32_t* vr = vidx.data() + (size_t)h->rows[i] * Kx;
+        int32_t first = -1, count = 0;
+        for (int x = 0; x < Kx; ++x)
+            if (vr[x] >= 0) {
+                if (first < 0) first = vr[x];
+                if (vr[x] != first + count) return set_err(h, SVH_ERR_STATE, "svh_setup_grid: voxel order");
+                ++count;
+            }
+        rinfo[2 * i] = first;
+        rinfo[2 * i + 1] = count;
+    }
+    for (int64_t v = 0; v < K; ++v) vx[v] = (int32_t)(h->vox[v] % Kx);
     h->Px = default_fft_size(Kx, false); h->Py = default_fft_size(Ky, false); h->Pz = default_fft_size(Kz, true);
     h->Hx = h->Px / 2 + 1; h->Hy = h->Py / 2 + 1; h->Hz = h->Pz / 2 + 1;
     std::vector<uint8_t> freem(M);
@@ -671,6 +686,8 @@ int svh_setup_grid(svh_handle* hh, int Kx, int Ky, int Kz, double dx, const uint
     int rc;
     if ((rc = dev_upload(h, h->d_vidx, vidx.data(), vidx.size() * 4))) return rc;
     if ((rc = dev_upload(h, h->d_rows, h->rows.data(), h->rows.size() * 4))) return rc;
+    if ((rc = dev_upload(h, h->d_rinfo, rinfo.data(), rinfo.size() * 4))) return rc;
+    if ((rc = dev_upload(h, h->d_vx, vx.data(), vx.size() * 4))) return rc;
     if ((rc = dev_upload(h, h->d_rowmask, rowmask.data(), rowmask.size()))) return rc;
     if ((rc = dev_upload(h, h->d_zlist, h->zlist.data(), h->zlist.size() * 4))) return rc;
     if ((rc = dev_upload(h, h->d_node, h->node.data(), h->node.size() * 4))) return rc;

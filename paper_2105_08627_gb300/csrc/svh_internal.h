@@ -49,6 +49,8 @@ struct Handle {
     // device copies
     DevBuf d_vidx;      // int32 [nza][Ky][Kx]  voxel index or -1
     DevBuf d_rows;      // int32 [nrows]
+    DevBuf d_rinfo;     // int2 [nrows]: first voxel index and voxel count of each active row
+    DevBuf d_vx;        // int32 [K]: x of each voxel (a row's voxels are consecutive, ordered by x)
     DevBuf d_rowmask;   // uint8 [nza][Ky] 1 for rows holding voxels
     DevBuf d_zlist;     // int32 [nza]
     DevBuf d_node;      // int32 [K*6]
