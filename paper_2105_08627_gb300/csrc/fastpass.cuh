@@ -243,6 +243,22 @@ __global__ void __launch_bounds__(NT) k_xinv_grouped(const __grid_constant__ Pas
     const int64_t ngroups = (int64_t)a.nb * a.nrows;
     const int64_t g0 = (int64_t)blockIdx.x * G;
     const int Kx = a.Kx;
+    // the first epilogue task's per-voxel data (x, lambda, sigma0, face nodes) of group 0, loaded
+    // now so that the loads overlap the transforms
+    int pf_vi = -1, pf_x = 0, pf_nd[6];
+    T pf_lm = 0, pf_s0 = 0;
+    if (g0 < ngroups) {
+        const int64_t b = g0 / a.nrows;
+        const int2 ri = a.rinfo[g0 - b * a.nrows];
+        if ((int)threadIdx.x < ri.y) {
+            pf_vi = ri.x + (int)threadIdx.x;
+            pf_x = __ldg(a.vx + pf_vi);
+            pf_lm = (T)a.lam[pf_vi];
+            pf_s0 = (T)a.sig0[pf_vi];
+#pragma unroll
+            for (int f = 0; f < 6; ++f) pf_nd[f] = __ldg(a.node + (int64_t)pf_vi * 6 + f);
+        }
+    }
     {
         const int l = threadIdx.x / N2, n2 = threadIdx.x % N2;
         const int64_t g = g0 + l / 5;
@@ -305,12 +321,13 @@ __global__ void __launch_bounds__(NT) k_xinv_grouped(const __grid_constant__ Pas
         const int64_t b = g / a.nrows;
         const int2 ri = a.rinfo[g - b * a.nrows];
         for (int j = threadIdx.x; j < ri.y; j += NT) {
+            const bool pf = gl == 0 && j == (int)threadIdx.x;   // data loaded at the start
             const int vi = ri.x + j;
-            const int x = __ldg(a.vx + vi);
+            const int x = pf ? pf_x : __ldg(a.vx + vi);
             const double om = a.omegas ? a.omegas[b] : a.omega;
             const T cs = a.omegas ? (T)(om * a.mu * a.dx * a.inv_P) : (T)a.conv_scale;
             // two-fluid c = a + j omega mu b (Eq. 22-23), once per voxel
-            const T lm = (T)a.lam[vi], s0 = (T)a.sig0[vi];
+            const T lm = pf ? pf_lm : (T)a.lam[vi], s0 = pf ? pf_s0 : (T)a.sig0[vi];
             const T wm = (T)(om * a.mu);
             const T wml2 = wm * lm * lm;
             const T tt = s0 * wml2;
@@ -322,7 +339,7 @@ __global__ void __launch_bounds__(NT) k_xinv_grouped(const __grid_constant__ Pas
             const int32_t* nd = a.node + (int64_t)vi * 6;
 #pragma unroll
             for (int f = 0; f < 6; ++f) {
-                const int m = nd[f];
+                const int m = pf ? pf_nd[f] : nd[f];
                 if (!a.masked || a.freem[m]) ph[f] = xb[5 * a.K + m];
                 else { ph[f].x = 0; ph[f].y = 0; }
             }
