@@ -370,8 +370,11 @@ __global__ void __launch_bounds__(NT) k_xinv_grouped(const __grid_constant__ Pas
 // ---------------------------------------------------------------- y passes (strided lines, kx tiles)
 // INV = false: B1 rows y < Ky (active) -> forward FFT -> B2 rows ky < Py.
 // INV = true : B2 -> inverse FFT -> B1 active rows y < Ky.
+// (256-thread blocks of lines up to 32 x 32 points: registers capped so that three blocks share
+// an SM and one block's loads overlap another's transforms)
 template <typename T, int N1, int N2, bool INV, int NT>
-__global__ void __launch_bounds__(NT) k_ycol_fast(const __grid_constant__ PassArgs a) {
+__global__ void __launch_bounds__(NT, (NT == 256 && N1 <= 32) ? 3 : 1)
+    k_ycol_fast(const __grid_constant__ PassArgs a) {
     using C = typename CT<T>::type;
     constexpr int N = N1 * N2;
     constexpr int TB = NT / N2;           // kx columns per block
