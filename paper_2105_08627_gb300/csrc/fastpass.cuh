@@ -130,7 +130,9 @@ __global__ void __launch_bounds__(NT) k_xrow(const __grid_constant__ PassArgs a)
     C* tw = reinterpret_cast<C*>(smem_raw);
     C* buf = tw + N;
     const C* twg = static_cast<const C*>(a.twx);
-    for (int i = threadIdx.x; i < N; i += NT) tw[i] = twg[i];
+    // twiddles of the N1 x N2 step in [k1][n2] order: tw[k1 N2 + n2] = W^(n2 k1) (n2 k1 < N), so a
+    // thread's N1 factors sit at constant offsets and a warp's lanes read consecutive entries
+    for (int i = threadIdx.x; i < N; i += NT) tw[i] = twg[(i / N2) * (i % N2)];
     const int64_t line0 = (int64_t)blockIdx.x * L;
     {
         const int l = threadIdx.x / N2, n2 = threadIdx.x % N2;
@@ -177,8 +179,8 @@ __global__ void __launch_bounds__(NT) k_xrow(const __grid_constant__ PassArgs a)
         __syncthreads();   // twiddle table ready
 #pragma unroll
         for (int k1 = 1; k1 < N1; ++k1) {
-            const int m = (n2 * k1) % N;
-            if (m) v[k1] = INV ? cmulc(v[k1], tw[m]) : cmul(v[k1], tw[m]);
+            const C w = tw[k1 * N2 + n2];   // 1 for n2 = 0
+            v[k1] = INV ? cmulc(v[k1], w) : cmul(v[k1], w);
         }
 #pragma unroll
         for (int k1 = 0; k1 < N1; ++k1) buf[(l * N2 + n2) * LDS + k1] = v[k1];
@@ -239,7 +241,9 @@ __global__ void __launch_bounds__(NT) k_xinv_grouped(const __grid_constant__ Pas
     C* tw = reinterpret_cast<C*>(smem_raw);
     C* buf = tw + N;
     const C* twg = static_cast<const C*>(a.twx);
-    for (int i = threadIdx.x; i < N; i += NT) tw[i] = twg[i];
+    // twiddles of the N1 x N2 step in [k1][n2] order: tw[k1 N2 + n2] = W^(n2 k1) (n2 k1 < N), so a
+    // thread's N1 factors sit at constant offsets and a warp's lanes read consecutive entries
+    for (int i = threadIdx.x; i < N; i += NT) tw[i] = twg[(i / N2) * (i % N2)];
     const int64_t ngroups = (int64_t)a.nb * a.nrows;
     const int64_t g0 = (int64_t)blockIdx.x * G;
     const int Kx = a.Kx;
@@ -278,8 +282,7 @@ __global__ void __launch_bounds__(NT) k_xinv_grouped(const __grid_constant__ Pas
         __syncthreads();
 #pragma unroll
         for (int k1 = 1; k1 < N1; ++k1) {
-            const int m = (n2 * k1) % N;
-            if (m) v[k1] = cmulc(v[k1], tw[m]);
+            v[k1] = cmulc(v[k1], tw[k1 * N2 + n2]);   // 1 for n2 = 0
         }
 #pragma unroll
         for (int k1 = 0; k1 < N1; ++k1) buf[(l * N2 + n2) * LDS + k1] = v[k1];
@@ -373,7 +376,7 @@ __global__ void __launch_bounds__(NT) k_xinv_grouped(const __grid_constant__ Pas
 // (256-thread blocks of lines up to 32 x 32 points: registers capped so that three blocks share
 // an SM and one block's loads overlap another's transforms)
 template <typename T, int N1, int N2, bool INV, int NT>
-__global__ void __launch_bounds__(NT, (NT == 256 && N1 <= 32) ? 3 : 1)
+__global__ void __launch_bounds__(NT, (NT == 256 && N1 <= 32) ? 3 : 0)
     k_ycol_fast(const __grid_constant__ PassArgs a) {
     using C = typename CT<T>::type;
     constexpr int N = N1 * N2;
@@ -383,6 +386,8 @@ __global__ void __launch_bounds__(NT, (NT == 256 && N1 <= 32) ? 3 : 1)
     C* tw = reinterpret_cast<C*>(smem_raw);
     C* buf = tw + N;                      // [n2][k1][TB]
     const C* twg = static_cast<const C*>(a.twy);
+    // twiddles of the N1 x N2 step in natural order, read at m = n2 k1 (with 512-thread blocks the
+    // [k1][n2] order of the other passes measured slower here)
     for (int i = threadIdx.x; i < N; i += NT) tw[i] = twg[i];
     const int kx0 = blockIdx.x * TB;
     const int zi = blockIdx.y;
@@ -482,7 +487,9 @@ __global__ void __launch_bounds__(NT, 2) k_ycol_async(const __grid_constant__ Pa
     C* in = tw + N;                              // [NROW][TB]
     C* buf = in + NROW * TB;                     // [n2][k1][TB]
     const C* twg = static_cast<const C*>(a.twy);
-    for (int i = threadIdx.x; i < N; i += NT) tw[i] = twg[i];
+    // twiddles of the N1 x N2 step in [k1][n2] order: tw[k1 N2 + n2] = W^(n2 k1) (n2 k1 < N), so a
+    // thread's N1 factors sit at constant offsets and a warp's lanes read consecutive entries
+    for (int i = threadIdx.x; i < N; i += NT) tw[i] = twg[(i / N2) * (i % N2)];
     const int Px = a.Px, Ky = a.Ky, nza = a.nza;
     const int nkx = (Px + TB - 1) / TB;
     // the launcher takes this kernel only when Px is a multiple of TB: a tile's columns are all in range
@@ -529,8 +536,8 @@ __global__ void __launch_bounds__(NT, 2) k_ycol_async(const __grid_constant__ Pa
         if (t + (int)gridDim.x < ntiles) issue(t + gridDim.x);   // the next tile's rows, in flight
 #pragma unroll
         for (int k1 = 1; k1 < N1; ++k1) {
-            const int m = (n2 * k1) % N;
-            if (m) v[k1] = INV ? cmulc(v[k1], tw[m]) : cmul(v[k1], tw[m]);
+            const C w = tw[k1 * N2 + n2];   // 1 for n2 = 0
+            v[k1] = INV ? cmulc(v[k1], w) : cmul(v[k1], w);
         }
 #pragma unroll
         for (int k1 = 0; k1 < N1; ++k1) buf[(n2 * N1 + k1) * TB + c] = v[k1];
