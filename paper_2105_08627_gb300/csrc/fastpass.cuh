@@ -249,8 +249,11 @@ __global__ void __launch_bounds__(NT) k_xinv_grouped(const __grid_constant__ Pas
     const int Kx = a.Kx;
     // the first epilogue task's per-voxel data (x, lambda, sigma0, face nodes) of group 0, loaded
     // now so that the loads overlap the transforms
+    // (FP32 also its input values and face-node potentials: the FP64 form has no registers to spare)
+    constexpr bool PFV = std::is_same<T, float>::value;
     int pf_vi = -1, pf_x = 0, pf_nd[6];
     T pf_lm = 0, pf_s0 = 0;
+    C pf_I[5], pf_ph[6];
     if (g0 < ngroups) {
         const int64_t b = g0 / a.nrows;
         const int2 ri = a.rinfo[g0 - b * a.nrows];
@@ -259,6 +262,11 @@ __global__ void __launch_bounds__(NT) k_xinv_grouped(const __grid_constant__ Pas
             pf_x = __ldg(a.vx + pf_vi);
             pf_lm = (T)a.lam[pf_vi];
             pf_s0 = (T)a.sig0[pf_vi];
+            if constexpr (PFV) {
+                const C* xb = static_cast<const C*>(a.x) + b * a.Nvec;
+#pragma unroll
+                for (int be = 0; be < 5; ++be) pf_I[be] = xb[be * a.K + pf_vi];
+            }
 #pragma unroll
             for (int f = 0; f < 6; ++f) pf_nd[f] = __ldg(a.node + (int64_t)pf_vi * 6 + f);
         }
@@ -277,6 +285,15 @@ __global__ void __launch_bounds__(NT) k_xinv_grouped(const __grid_constant__ Pas
         } else {
 #pragma unroll
             for (int n1 = 0; n1 < N1; ++n1) { v[n1].x = 0; v[n1].y = 0; }
+        }
+        if (PFV && pf_vi >= 0) {   // the prefetched voxel's face-node potentials (need its node indices)
+            const C* xb = static_cast<const C*>(a.x) + (g0 / a.nrows) * a.Nvec;
+#pragma unroll
+            for (int f = 0; f < 6; ++f) {
+                const int m = pf_nd[f];
+                if (!a.masked || a.freem[m]) pf_ph[f] = xb[5 * a.K + m];
+                else { pf_ph[f].x = 0; pf_ph[f].y = 0; }
+            }
         }
         reg_fft<N1, true>(v);
         __syncthreads();
@@ -342,9 +359,13 @@ __global__ void __launch_bounds__(NT) k_xinv_grouped(const __grid_constant__ Pas
             const int32_t* nd = a.node + (int64_t)vi * 6;
 #pragma unroll
             for (int f = 0; f < 6; ++f) {
-                const int m = pf ? pf_nd[f] : nd[f];
-                if (!a.masked || a.freem[m]) ph[f] = xb[5 * a.K + m];
-                else { ph[f].x = 0; ph[f].y = 0; }
+                if (PFV && pf) {
+                    ph[f] = pf_ph[f];
+                } else {
+                    const int m = nd[f];
+                    if (!a.masked || a.freem[m]) ph[f] = xb[5 * a.K + m];
+                    else { ph[f].x = 0; ph[f].y = 0; }
+                }
             }
 #pragma unroll
             for (int be = 0; be < 5; ++be) {
@@ -353,7 +374,7 @@ __global__ void __launch_bounds__(NT) k_xinv_grouped(const __grid_constant__ Pas
                 val.x = -cs * cv.y;
                 val.y = cs * cv.x;
                 const T sb = be < 3 ? (T)1 : (be == 3 ? (T)(1.0 / 6.0) : (T)0.5);
-                const C I = xb[be * a.K + vi];
+                const C I = (PFV && pf) ? pf_I[be] : xb[be * a.K + vi];
                 val.x += sb * (cre * I.x - cim * I.y);
                 val.y += sb * (cre * I.y + cim * I.x);
 #pragma unroll
