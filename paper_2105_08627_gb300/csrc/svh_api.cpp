@@ -136,9 +136,9 @@ static void free_all(Handle* h) {
     free_kernels(h);
     prof_release(h);
     precond_free(h);
-    for (DevBuf* b : {&h->d_vidx, &h->d_rows, &h->d_rinfo, &h->d_vx, &h->d_rowmask, &h->d_zlist, &h->d_node, &h->d_ninc,
-                      &h->d_free, &h->d_lam, &h->d_sig0, &h->d_B1, &h->d_B2, &h->d_xin, &h->d_yout, &h->d_omegas,
-                      &h->d_status})
+    for (DevBuf* b : {&h->d_vidx, &h->d_rows, &h->d_rinfo, &h->d_vx, &h->d_rowmask, &h->d_zlist, &h->d_node,
+                      &h->d_ninc, &h->d_free, &h->d_lam, &h->d_sig0, &h->d_B1, &h->d_B2, &h->d_xin, &h->d_yout,
+                      &h->d_omegas, &h->d_status})
         dev_free(*b);
 }
 
