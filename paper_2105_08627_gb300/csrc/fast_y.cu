@@ -32,7 +32,10 @@ template <int N1, int N2, bool INV, int NT>
 static void run_y_async(const PassArgs& a, cudaStream_t s) {
     constexpr int TB = NT / N2;
     constexpr int N = N1 * N2;
-    const size_t sm = (size_t)(N + (INV ? N : N / 2) * TB + N * TB) * sizeof(float2);
+    // forward: room for the planes' active-row bits when they take at most 4 KB
+    const int wpp = (a.Ky + 31) / 32;
+    const int rbw = (!INV && (size_t)a.nza * wpp * 4 <= 4096) ? wpp : 0;
+    const size_t sm = (size_t)(N + (INV ? N : N / 2) * TB + N * TB) * sizeof(float2) + (size_t)a.nza * rbw * 4;
     cudaFuncSetAttribute(k_ycol_async<N1, N2, INV, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
@@ -40,7 +43,7 @@ static void run_y_async(const PassArgs& a, cudaStream_t s) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ycol_async<N1, N2, INV, NT>, NT, sm);
     const int ntiles = ((a.Px + TB - 1) / TB) * a.nza * a.nb * 5;
     const int grid = std::max(1, std::min(ntiles, std::max(1, sms) * std::max(1, per_sm)));
-    k_ycol_async<N1, N2, INV, NT><<<grid, NT, sm, s>>>(a, ntiles);
+    k_ycol_async<N1, N2, INV, NT><<<grid, NT, sm, s>>>(a, ntiles, rbw);
 }
 
 // N1 x N2 default split; SWAP: the transposed split is a variant too

@@ -494,7 +494,7 @@ __global__ void __launch_bounds__(NT, (NT == 256 && N1 <= 32) ? 3 : 0)
 // first stage has read the current tile from it, the copies of the block's NEXT tile are issued,
 // so they land while this tile is twiddled, exchanged, transformed and stored.
 template <int N1, int N2, bool INV, int NT>
-__global__ void __launch_bounds__(NT, 2) k_ycol_async(const __grid_constant__ PassArgs a, int ntiles) {
+__global__ void __launch_bounds__(NT, 2) k_ycol_async(const __grid_constant__ PassArgs a, int ntiles, int rbw_arg) {
     using C = float2;
     constexpr int N = N1 * N2;
     constexpr int TB = NT / N2;                 // kx columns per tile (even)
@@ -507,6 +507,10 @@ __global__ void __launch_bounds__(NT, 2) k_ycol_async(const __grid_constant__ Pa
     C* tw = reinterpret_cast<C*>(smem_raw);
     C* in = tw + N;                              // [NROW][TB]
     C* buf = in + NROW * TB;                     // [n2][k1][TB]
+    // forward: the active-row masks of every plane as bits ([plane][Ky / 32] words), when the
+    // launcher gave them room (rbw > 0), so that a copy's row test is a shared-memory read
+    uint32_t* rbits = reinterpret_cast<uint32_t*>(buf + N * TB);
+    const int rbw = INV ? 0 : rbw_arg;
     const C* twg = static_cast<const C*>(a.twy);
     // twiddles of the N1 x N2 step in [k1][n2] order: tw[k1 N2 + n2] = W^(n2 k1) (n2 k1 < N), so a
     // thread's N1 factors sit at constant offsets and a warp's lanes read consecutive entries
@@ -526,13 +530,22 @@ __global__ void __launch_bounds__(NT, 2) k_ycol_async(const __grid_constant__ Pa
             const int e = threadIdx.x + i * NT;
             if (e < NROW * SEG) {
                 const int row = e / SEG, sg = e % SEG;
-                const bool valid = INV || (row < Ky && __ldg(rm + row));
+                const bool valid =
+                    INV || (row < Ky && (rbw ? (rbits[zi * rbw + (row >> 5)] >> (row & 31)) & 1u : __ldg(rm + row)));
                 cp_async16_zfill(in + row * TB + 2 * sg, src + (int64_t)(valid ? row : 0) * Px + 2 * sg, valid);
             }
         }
         cp_async_commit();
     };
     const int c = threadIdx.x % TB, n2 = threadIdx.x / TB;
+    for (int w = threadIdx.x; w < nza * rbw; w += NT) {
+        const int zi = w / rbw, y0 = (w % rbw) * 32;
+        const uint8_t* rm = a.rowmask + (int64_t)zi * Ky;
+        uint32_t bits = 0;
+        for (int b = 0; b < 32 && y0 + b < Ky; ++b) bits |= (uint32_t)(__ldg(rm + y0 + b) != 0) << b;
+        rbits[w] = bits;
+    }
+    __syncthreads();
     int t = blockIdx.x;
     if (t < ntiles) issue(t);
     cp_async_wait<0>();
