@@ -355,10 +355,11 @@ int svh_matvec_noalloc(svh_handle* h, double omega, int nb, const void* x_dev, v
  * active planes are contiguous). Choice 6 is the stream schedule of a
  * product: 0 runs the Tucker restore and the node rows on the handle's second
  * stream, overlapping passes 1-2; 1 overlaps only the node rows; 2 uses one
- * stream. svh_autotune times every variant of every pass on this handle's
+ * stream; 3 overlaps the node rows with pass 1 only (joined before pass 2, so
+ * that a persistent y pass starts on every SM). svh_autotune times every variant of every pass on this handle's
  * grid for nb right-hand sides (zero data, 5 launches each, CUDA events on
  * the handle's stream), then the fused path against the separate passes,
- * then the three schedules on whole products, and keeps the fastest for
+ * then the four schedules on whole products, and keeps the fastest for
  * later FP32 products; results are cached per process for equal grids and
  * nb. variants[7] and ms[7] (may be NULL) receive the choices and their
  * milliseconds per launch. svh_set_pass_variant forces one (SVH_ERR_ARG if

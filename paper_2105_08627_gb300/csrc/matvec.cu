@@ -535,7 +535,8 @@ static int run_matvec(Handle* h, double omega, const double* d_omegas, int nb, c
         SVH_CUDA_TRY(h, cudaStreamWaitEvent(sa, h->ev_fork, 0));
     }
     // stream schedule (tuned): 0 restore and node rows on the second stream, 1 node rows
-    // only (restore first on this stream), 2 everything on this stream
+    // only (restore first on this stream), 2 everything on this stream, 3 as 1 with the node rows
+    // joined before pass 2 (they overlap pass 1 only: a persistent y pass then has every SM)
     // (the host-buffer entry point always overlaps the restore with its input copy)
     const int sched = preforked ? 0 : h->tune32[6];
     cudaStream_t s_rb = sched == 0 ? sa : s, s_nd = sched == 2 ? s : sa;
@@ -556,7 +557,7 @@ static int run_matvec(Handle* h, double omega, const double* d_omegas, int nb, c
     prof_at(h, 0, 1, s_rb);
     cudaEventRecord(h->ev_spec, s_rb);
     if (preforked && s_nd == sa) cudaStreamWaitEvent(sa, h->ev_x, 0);   // the node rows read the input
-    if (sched == 1) {   // the node rows fork after the restore
+    if (sched == 1 || sched == 3) {   // the node rows fork after the restore
         cudaEventRecord(h->ev_fork, s);
         cudaStreamWaitEvent(sa, h->ev_fork, 0);
     }
@@ -577,6 +578,7 @@ static int run_matvec(Handle* h, double omega, const double* d_omegas, int nb, c
         prof_at(h, 2, 0, s);
         prof_at(h, 2, 1, s);
         cudaStreamWaitEvent(s, h->ev_spec, 0);
+        if (sched == 3) cudaStreamWaitEvent(s, h->ev_done, 0);
         prof_at(h, 3, 0, s);
         launch_yz(pa, h->smem_optin, s);
         prof_at(h, 3, 1, s);
@@ -599,7 +601,8 @@ static int run_matvec(Handle* h, double omega, const double* d_omegas, int nb, c
                                              nlines);
         }
         prof_at(h, 1, 1, s);
-        // pass 2
+        // pass 2 (schedule 3: after the node rows)
+        if (sched == 3) cudaStreamWaitEvent(s, h->ev_done, 0);
         prof_at(h, 2, 0, s);
         int tby = std::max(1, std::min(32, MAXPTS * NTHR / Py));
         pa.var = var(1);
@@ -701,7 +704,7 @@ int launch_matvec_on(Handle* h, double omega, int nb, const void* x, void* y, in
 static int pass_variants(const Handle* h, int p, const PassArgs* pa = nullptr) {
     switch (p) {
         case 5: return pa && fused_path_ok(*pa, h->smem_optin) ? 2 : 1;
-        case 6: return 3;
+        case 6: return 4;
         case 0: return x_fast_variants(h->Px, false, true);
         case 1: return y_fast_variants(h->Py, true);
         case 2: {   // 0-2 FFT forms, 3 direct (fast_zd.cu), 4-6 split pencils (fast_zs.cu)
@@ -824,8 +827,8 @@ int autotune(Handle* h, int nb, int32_t* variants, double* ms) {
     if (variants) variants[5] = best[5];
     // 6: the stream schedule, timed on whole products (with the restore in rebuild mode)
     {
-        float t[3] = {0, 0, 0};
-        for (int v = 0; v < 3; ++v) {
+        float t[4] = {0, 0, 0, 0};
+        for (int v = 0; v < 4; ++v) {
             h->tune32[6] = v;
             int rc = launch_matvec<float>(h, 2e9, nb, x.p, y.p, 0, nullptr);
             cudaEventRecord(e0, s);
@@ -834,10 +837,10 @@ int autotune(Handle* h, int nb, int32_t* variants, double* ms) {
             if (rc || cudaEventSynchronize(e1) != cudaSuccess) return done(rc ? rc : SVH_ERR_CUDA);
             cudaEventElapsedTime(&t[v], e0, e1);
         }
-        // whole products on zero data are noisier than single passes: leave the
-        // node-rows-only schedule (1) for another one only on a clear (2 %) win
-        best[6] = 1;
-        for (int v : {0, 2})
+        // whole products on zero data are noisier than single passes: leave schedule 3 (node
+        // rows beside pass 1 only) for another one only on a clear (2 %) win
+        best[6] = 3;
+        for (int v : {0, 1, 2})
             if (t[v] < 0.98f * t[best[6]]) best[6] = v;
         h->tune32[6] = best[6];
         if (variants) variants[6] = best[6];

@@ -122,7 +122,8 @@ struct Handle {
     DevBuf d_omegas;                   // per-item frequencies for svh_matvec_omegas
     DevBuf d_status;                   // int32 status word set by kernels (bounded waits that expired)
     // FP32 tile variant per FFT pass; [5]: 0 separate passes, 1 fused y/z/y; [6] stream
-    // schedule: 0 restore + node rows on the second stream, 1 node rows only, 2 one stream
+    // schedule: 0 restore + node rows on the second stream, 1 node rows only, 2 one stream,
+    // 3 node rows beside pass 1 only
     int tune32[7] = {0, 0, 0, 0, 0, 0, 0};
     size_t smem_optin = 0;                // opt-in shared memory per block of the device
 };

@@ -507,7 +507,7 @@ class Handle:
     def pass_variants(self):
         """-> (number of variants per FFT pass (0: generic kernel), current choice);
         entry 5 is the path (2 choices when the fused y/z/y kernel applies), entry 6 the
-        stream schedule (3 choices)."""
+        stream schedule (4 choices)."""
         n = np.zeros(7, np.int32)
         c = np.zeros(7, np.int32)
         self._ck(lib().svh_get_pass_variants(self._h, _i32p(n), _i32p(c)), "svh_get_pass_variants")

@@ -179,7 +179,7 @@ def test_tucker_rebuild_matches_oracle_restore():
     _check_fp32(y, yref)
     # rebuild-every-matvec mode gives the same result, in every stream schedule
     h.set_kernel_mode(svh.SVH_KERNELS_TUCKER_REBUILD)
-    for sched in (0, 1, 2):
+    for sched in (0, 1, 2, 3):
         h.set_pass_variant(6, sched)
         y2 = h.matvec(om, torch.from_numpy(x.astype(np.complex64)).cuda()).cpu().numpy().astype(np.complex128)
         assert np.array_equal(y, y2), sched
@@ -389,8 +389,8 @@ def test_every_tile_variant_and_autotune(seed, shape, fused):
             assert h.device_status() == 0          # no bounded wait (TMA z pass) expired
         h.set_pass_variant(p, 0)
     h.set_pass_variant(5, 0)
-    assert counts[6] == 3
-    for v in (1, 2, 0):                                                         # stream schedules
+    assert counts[6] == 4
+    for v in (1, 2, 3, 0):                                                      # stream schedules
         h.set_pass_variant(6, v)
         _check_fp32(h.matvec(om, xd).cpu().numpy().astype(np.complex128), yref)
     with pytest.raises(Exception):
