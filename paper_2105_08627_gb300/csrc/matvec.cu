@@ -578,7 +578,7 @@ static int run_matvec(Handle* h, double omega, const double* d_omegas, int nb, c
         prof_at(h, 2, 0, s);
         prof_at(h, 2, 1, s);
         cudaStreamWaitEvent(s, h->ev_spec, 0);
-        if (sched == 3) cudaStreamWaitEvent(s, h->ev_done, 0);
+        if (sched == 3 || preforked) cudaStreamWaitEvent(s, h->ev_done, 0);
         prof_at(h, 3, 0, s);
         launch_yz(pa, h->smem_optin, s);
         prof_at(h, 3, 1, s);
@@ -601,8 +601,8 @@ static int run_matvec(Handle* h, double omega, const double* d_omegas, int nb, c
                                              nlines);
         }
         prof_at(h, 1, 1, s);
-        // pass 2 (schedule 3: after the node rows)
-        if (sched == 3) cudaStreamWaitEvent(s, h->ev_done, 0);
+        // pass 2 (schedule 3 and the host-buffer entry point: after the second stream's work)
+        if (sched == 3 || preforked) cudaStreamWaitEvent(s, h->ev_done, 0);
         prof_at(h, 2, 0, s);
         int tby = std::max(1, std::min(32, MAXPTS * NTHR / Py));
         pa.var = var(1);
