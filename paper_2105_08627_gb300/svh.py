@@ -487,7 +487,8 @@ class Handle:
         """Time every FP32 tile variant of the five FFT passes for nb items, then the
         fused y/z/y path against the separate passes, then the stream schedules, and
         keep the fastest -> (variants[7], ms per launch[7]); variants[5]: 0 separate passes,
-        1 fused; variants[6]: 0 restore + node rows overlapped, 1 node rows only, 2 one stream.
+        1 fused; variants[6]: 0 restore + node rows overlapped, 1 node rows only, 2 one stream,
+        3 node rows beside the x forward pass only.
         timings=False asks for no timings (ms is None), so that an equal grid tuned earlier in
         the process is taken from the cache without timing anything."""
         v = np.zeros(7, np.int32)
